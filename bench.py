@@ -1,0 +1,365 @@
+#!/usr/bin/env python3
+"""Benchmark: brute-force dedispersion of one Apertif-like beam per GPU.
+
+Workload (one step = one full forward pass, Algorithm 1, over one beam):
+1024 channels from 1420 MHz at 0.29296875 MHz, 50 us sampling, 2048 DM
+trials from 0 in steps of 0.25, 20,000 output samples (one second) -- the
+Apertif setup of Table 2.  Input: seeded synthetic N(0,1) float32 (or
+round(N(128,16)) uint8 with --dtype u8) with 3 injected dispersed pulses.
+
+Prints one JSON line.  ``value`` is DM-trial x samples per second over all
+ranks (each rank dedisperses its own beam: weak scaling, no collective on the
+data path).  ``roofline`` reports the dominant kernel against the roof that
+binds it; ``e2e`` measures the same metric through dd_forward_host with
+host buffers (copies inside the timed region); ``cpu_baseline`` times the
+oracle on a bounded sample of the same workload on this host's cores.
+
+--impl reference times the oracle itself as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1601_01165_gb300 import synth  # noqa: E402
+
+METRIC = "dedispersed DM-trial·samples/s and achieved HBM GB/s (fraction of roofline), 1 GB300"
+UNIT = "DM-trial·samples/s"
+L2_BYTES = 129 * 1024 * 1024
+SMS = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+# DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
+# keyed by (kernel config, dtype); valid only while the kernel source hash matches.
+NCU_TRAFFIC = {}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), float(m.get("sm_max_mhz", SM_MAX_MHZ_NOMINAL)), "measured"
+    except Exception:
+        return 6800.0, SM_MAX_MHZ_NOMINAL, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1601_01165_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi sampler for SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.active = False
+        self.ready = threading.Event()
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            self.ready.set()
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+        self.ready.wait(timeout=10)
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.ready.set()
+            if self.active:
+                self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        self.active = False
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, n in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows),
+                "power_w_max": max((float(r[2]) for r in self.rows if _isnum(r[2])), default=None)}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline(setup, dtype, target_s=12.0, seed=0):
+    """Time the oracle (as it stands, single thread) on a bounded sample of the workload:
+    a subset of DM trials spread over the whole range, every channel, all samples."""
+    import oracle
+    oracle.build()
+    d = oracle.delay_table(*setup.plan_args()[:7])
+    n_in = setup.n_out + int(d.max())
+    x = (synth.noise_u8 if dtype == "u8" else synth.noise_f32)(seed, setup.channels, n_in)
+    fwd = (lambda dd: oracle.forward_u8(dd, x, setup.n_out)) if dtype == "u8" else \
+        (lambda dd: oracle.forward_f32(dd, x, setup.n_out))
+    t = time.perf_counter()
+    fwd(d[:1])
+    per_row = max(time.perf_counter() - t, 1e-4)
+    rows = int(max(1, min(setup.n_dm, target_s / per_row)))
+    idx = np.linspace(0, setup.n_dm - 1, rows).astype(np.int64)
+    sub = np.ascontiguousarray(d[idx])
+    t = time.perf_counter()
+    fwd(sub)
+    el = time.perf_counter() - t
+    return {"value": rows * setup.n_out / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{rows} of {setup.n_dm} DM trials (evenly spaced) x {setup.n_out} samples x "
+                      f"{setup.channels} channels, {dtype}, single-threaded C oracle, {el:.1f} s"}
+
+
+def run_reference(args, setup):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    d = oracle.delay_table(*setup.plan_args()[:7])
+    n_in = setup.n_out + int(d.max())
+    x = (synth.noise_u8 if args.dtype == "u8" else synth.noise_f32)(0, setup.channels, n_in)
+    fwd = (lambda dd: oracle.forward_u8(dd, x, setup.n_out)) if args.dtype == "u8" else \
+        (lambda dd: oracle.forward_f32(dd, x, setup.n_out))
+    t = time.perf_counter()
+    fwd(d[:1])
+    per_row = max(time.perf_counter() - t, 1e-4)
+    budget_per_step = 150.0 / max(1, args.steps + args.warmup)
+    rows = int(max(1, min(setup.n_dm, budget_per_step / per_row)))
+    rng = np.random.default_rng(1)
+    for _ in range(args.warmup):
+        fwd(np.ascontiguousarray(d[rng.choice(setup.n_dm, rows, replace=False)]))
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        fwd(np.ascontiguousarray(d[rng.choice(setup.n_dm, rows, replace=False)]))
+    el = time.perf_counter() - t
+    value = rows * setup.n_out * args.steps / el
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.dtype == "f32" else "int64", "data": "synthetic",
+        "config": _config(setup, args, None, None),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: {rows} random DM trials of {setup.n_dm} x {setup.n_out} "
+                                   f"samples x {setup.channels} channels, single-threaded C oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(setup, args, cfg_name, l2_note):
+    return {"workload": f"apertif-like single beam per GPU: {setup.channels} ch from {setup.f_low_mhz} MHz x "
+                        f"{setup.chan_bw_mhz} MHz, t_samp {setup.t_samp_s * 1e6:.0f} us, {setup.n_dm} DM trials "
+                        f"step {setup.dm_step}, {setup.n_out} output samples",
+            "dtype": args.dtype, "kernel_config": cfg_name, "l2": l2_note,
+            "parallelism": f"beams: one per GPU x {args.gpus}"}
+
+
+def run_ours(args, setup):
+    import torch
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    from paper_1601_01165_gb300 import binding as dd
+
+    plan = dd.Plan.from_setup(setup, args.dtype)
+    if args.config:
+        plan.select(args.config)
+    cfg_name = plan.selected
+    d = plan.delays()
+    stride = plan.padded_in_stride()
+    elem = 1 if args.dtype == "u8" else 4
+    in_bytes = setup.channels * stride * elem
+    n_buf = max(2, int(np.ceil(2 * L2_BYTES / in_bytes)) + 1)
+    host_x, _ = _make_input(setup, args.dtype, rank, plan.n_in, stride, d)
+    xs = [torch.from_numpy(host_x).to(dev) for _ in range(n_buf)]
+    out = torch.empty((setup.n_dm, setup.n_out), dtype=plan.out_dtype, device=dev)
+    stream = torch.cuda.current_stream()
+
+    for k in range(args.warmup):
+        plan.forward(xs[k % n_buf], out=out)
+    torch.cuda.synchronize()
+    if plan.device_status() != 0:
+        raise RuntimeError("device status nonzero after warm-up")
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.active = True
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for k in range(args.steps):
+        plan.forward(xs[k % n_buf], out=out)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    sampler.active = False
+    if ws > 1:
+        torch.distributed.barrier()
+    sampler.stop()
+    launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[args.steps])
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    units = setup.n_dm * setup.n_out * args.steps * ws
+    value = units / (total_ms / 1e3)
+
+    # end to end through the host-buffer entry point (pinned host memory, copies timed)
+    e2e = None
+    if not args.no_e2e:
+        hx = torch.from_numpy(np.ascontiguousarray(host_x[:, :plan.n_in])).pin_memory()
+        hout = torch.empty((setup.n_dm, setup.n_out), dtype=plan.out_dtype, pin_memory=True)
+        plan.forward_host(hx, out=hout)
+        ke = max(3, min(args.steps, 10))
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            plan.forward_host(hx, out=hout)
+        el = time.perf_counter() - t0
+        if ws > 1:
+            t = torch.tensor([el], device=dev, dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            el = float(t.item())
+        e2e = {"value": setup.n_dm * setup.n_out * ke * ws / el, "unit": UNIT,
+               "h2d_bytes_per_step": int(setup.channels * plan.n_in * elem),
+               "d2h_bytes_per_step": int(setup.n_dm * setup.n_out * 4), "steps": ke}
+
+    if plan.device_status() != 0:
+        raise RuntimeError("device status nonzero after timed region")
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    hbm_gbs, sm_max, peak_kind = _peaks()
+    avg_ms = statistics.fmean(launch_ms)
+    adds = setup.adds
+    compulsory = setup.channels * plan.n_in * elem + setup.n_dm * setup.n_out * 4 + 4 * setup.n_dm * setup.channels
+    add_peak = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12      # T adds/s
+    achieved_alu = adds / (avg_ms / 1e3) / 1e12
+    achieved_hbm = compulsory / (avg_ms / 1e3) / 1e9
+    kh = _kernel_hash()
+    tr = NCU_TRAFFIC.get((cfg_name, args.dtype))
+    traffic = tr["bytes"] if tr and tr.get("hash") == kh else None
+    roof = {"bound": "alu", "achieved": achieved_alu, "peak": add_peak,
+            "unit": "TFLOP/s" if args.dtype == "f32" else "Tops", "frac": achieved_alu / add_peak,
+            "traffic": traffic,
+            "peak_note": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz ({peak_kind} max clock), "
+                         f"1 add = 1 op (Eq. 2 counts one add per input sample)",
+            "per_launch_ops": adds, "avg_launch_ms": avg_ms,
+            "hbm": {"achieved_gbs": achieved_hbm, "peak_gbs": hbm_gbs, "frac": achieved_hbm / hbm_gbs,
+                    "compulsory_bytes": compulsory, "peak_kind": peak_kind}}
+    clocks = sampler.summary()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+        "config": _config(setup, args, cfg_name,
+                          f"{n_buf} rotating input buffers ({n_buf * in_bytes / 2**20:.0f} MiB > 2x L2)"),
+        "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
+        "kernel_source_hash": kh,
+        "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms)},
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(setup, args.dtype)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _make_input(setup, dtype, seed, n_in, stride, d):
+    x = (synth.noise_u8 if dtype == "u8" else synth.noise_f32)(seed, setup.channels, n_in, stride)
+    for i_p, t_p in synth.pulse_sites(seed, setup.n_dm, setup.n_out, 3):
+        synth.inject_pulse(x, d[i_p], t_p, 3, 40.0 if dtype == "u8" else 5.0)
+    return x, None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--dtype", choices=["f32", "u8"], default="f32")
+    ap.add_argument("--config", default=None, help="kernel configuration name (default: plan's choice)")
+    ap.add_argument("--workload", choices=["apertif", "lofar"], default="apertif")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    setup = synth.APERTIF if args.workload == "apertif" else synth.LOFAR
+    if args.impl == "reference":
+        return run_reference(args, setup)
+    return run_ours(args, setup)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

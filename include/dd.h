@@ -1,0 +1,265 @@
+/*
+ * libdd: brute-force incoherent dedispersion on NVIDIA GB300 (sm_103a).
+ *
+ * C ABI.  Every entry point takes plain host/device pointers and sizes; no C++
+ * or framework type crosses this boundary.  The method is the one of
+ * Sclocco et al., "Real-Time Dedispersion for Fast Radio Transient Surveys,
+ * using Auto Tuning on Many-Core Accelerators":
+ *
+ *   out[dm][t] = sum over c of w[c] * in[c][t + delay(c, dm)]      (Algorithm 1)
+ *   delay(c, dm) = round(4150 * DM * (1/f_c^2 - 1/f_h^2) / t_samp)   (Eq. 1)
+ *
+ * Conventions shared by every call:
+ *  - Frequencies in MHz, times in seconds, DM in pc cm^-3.  Channel c has
+ *    frequency f_low + c * chan_bw; channel 0 is the lowest, f_h is channel
+ *    C-1 (its delay is 0).  DM trial i is dm_first + i * dm_step.
+ *  - Delays are whole samples, Eq. 1 evaluated in IEEE double and rounded half
+ *    up (the paper does not say how to round).
+ *  - The input of one beam is a row-major [channels][in_row_stride] matrix
+ *    whose first n_in = n_out + max_delay samples per row are read (Section 2.1:
+ *    the t samples needed to produce s output samples).  The output is a
+ *    row-major [n_dm][out_row_stride] matrix; the first n_out entries of each
+ *    row are written.  Strides are in elements, not bytes.
+ *  - Data buffers (input, output, weights, gradients) are owned by the caller.
+ *    Plans, batches and stream states are owned by the library and freed by
+ *    their destroy call.
+ *  - Calls that take a `stream` (a cudaStream_t, NULL = legacy default stream)
+ *    are asynchronous: they enqueue work and return.  Pointers passed to them
+ *    must be device (or managed) memory of the plan's device unless the call
+ *    says "host".  Errors are returned as a status, never by aborting; a
+ *    human-readable detail for the last failing call on the calling thread is
+ *    available from dd_last_error().
+ *  - A plan is bound to the CUDA device that was current when it was made.
+ */
+#ifndef LIBDD_DD_H
+#define LIBDD_DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_plan_s* dd_plan_t;
+typedef struct dd_batch_s* dd_batch_t;
+typedef struct dd_stream_s* dd_stream_t;
+
+typedef enum {
+  DD_OK = 0,
+  DD_ERR_ARG = 1,          /* invalid argument: null pointer, non-positive size, bad value */
+  DD_ERR_SHAPE = 2,        /* a stride or length too small for the plan */
+  DD_ERR_ALIGN = 3,        /* pointer or stride alignment the call requires is not met */
+  DD_ERR_NOMEM = 4,        /* a device or host allocation failed */
+  DD_ERR_CUDA = 5,         /* a CUDA runtime call failed (detail in dd_last_error) */
+  DD_ERR_UNSUPPORTED = 6,  /* combination not supported (e.g. weights on the uint8 path) */
+  DD_ERR_BUDGET = 7,       /* request exceeds a memory budget */
+  DD_ERR_STATE = 8         /* object in the wrong state for the call */
+} dd_status;
+
+typedef enum {
+  DD_U8_I32 = 0,   /* uint8 samples, int32 sums, unit weights only: bit-exact */
+  DD_F32_F32 = 1   /* float32 samples and weights, float32 sums */
+} dd_dtype;
+
+/* ------------------------------------------------------------------ plans */
+
+/*
+ * Build a dedispersion plan: computes the delay table of Eq. 1 (Section 2)
+ * for n_dm trials x `channels` channels on the host in double precision,
+ * rounds it half up to whole samples, and uploads it with the tile
+ * descriptors the kernels use to the current device.  Section 2.1: the
+ * delays are computed once, in advance, and do not add to the O(d*s*c) cost.
+ *
+ * channels > 0, f_low_mhz > 0, chan_bw_mhz > 0, t_samp_s > 0, dm_first >= 0,
+ * dm_step >= 0, n_dm > 0, n_out > 0.  The largest delay must fit in int32 and
+ * the output sums must fit their type (uint8: channels * 255 < 2^31).
+ * Returns DD_ERR_ARG on bad values, DD_ERR_NOMEM / DD_ERR_CUDA on device
+ * failures.  *out is set only on DD_OK.
+ */
+dd_status dd_plan(dd_plan_t* out, int32_t channels, double f_low_mhz, double chan_bw_mhz,
+                  double t_samp_s, double dm_first, double dm_step, int32_t n_dm,
+                  int64_t n_out, dd_dtype dtype);
+
+/*
+ * Host-only: the delay table of Eq. 1 exactly as dd_plan computes it, written
+ * to `host_out` ([n_dm][channels] int32, row-major) without touching a GPU.
+ * Same argument rules and errors as dd_plan (DD_ERR_ARG).
+ */
+dd_status dd_delay_table(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                         double dm_first, double dm_step, int32_t n_dm, int32_t* host_out);
+
+/* Free a plan and its device memory.  NULL is accepted.  The caller must not
+ * destroy a plan while work enqueued with it may still run. */
+dd_status dd_plan_destroy(dd_plan_t plan);
+
+/*
+ * Sizes derived by the plan (any output pointer may be NULL):
+ *   n_in         input samples per channel row that are read, n_out + max_delay;
+ *   max_delay    the largest delay in samples (lowest channel, last DM trial);
+ *   device_bytes device memory the plan holds (delay table + descriptors).
+ */
+dd_status dd_plan_info(dd_plan_t plan, int64_t* n_in, int32_t* max_delay, int64_t* device_bytes);
+
+/* Copy the plan's delay table (Eq. 1, in samples) to host memory `host_out`,
+ * row-major [n_dm][channels] int32.  For checking the plan against Eq. 1. */
+dd_status dd_plan_delays(dd_plan_t plan, int32_t* host_out);
+
+/*
+ * Kernel selection.  A plan carries the tile configuration the forward call
+ * launches (the tunable parameters of Section 2.2: work per thread in DM and
+ * time, threads per block in DM and time, staging in shared memory or not).
+ * dd_plan_num_configs gives how many configurations are valid for the plan;
+ * dd_plan_config_name(plan, k) returns a static description of config k
+ * (NULL if out of range); dd_plan_select_config makes config k the one
+ * dd_forward uses; dd_plan_selected_config reports it.  A new plan starts at
+ * a built-in heuristic choice.
+ */
+dd_status dd_plan_num_configs(dd_plan_t plan, int32_t* n);
+const char* dd_plan_config_name(dd_plan_t plan, int32_t k);
+dd_status dd_plan_select_config(dd_plan_t plan, int32_t k);
+dd_status dd_plan_selected_config(dd_plan_t plan, int32_t* k);
+
+/*
+ * Failure detection.  Every wait inside the library's kernels is bounded
+ * (about one second); a wait that expires makes the kernel record a nonzero
+ * code in the plan's device status word and return early instead of hanging.
+ * This call waits for the device, reads that word into *code and clears it:
+ * DD_OK if it was 0, DD_ERR_STATE otherwise (1 = a bounded wait expired).
+ */
+dd_status dd_plan_device_status(dd_plan_t plan, int32_t* code);
+
+/* ---------------------------------------------------------------- forward */
+
+/*
+ * Algorithm 1 (Section 2.1) on one beam:
+ *   out[i][t] = sum_c w[c] * in[c][t + delay(c, i)],  0 <= i < n_dm, 0 <= t < n_out.
+ *
+ * in   device, [channels][in_row_stride] of uint8 (DD_U8_I32) or float
+ *      (DD_F32_F32); in_row_stride >= n_in.
+ * w    device float[channels] or NULL (unit weights).  Must be NULL for
+ *      DD_U8_I32 (DD_ERR_UNSUPPORTED otherwise).
+ * out  device, [n_dm][out_row_stride] of int32 (DD_U8_I32) or float;
+ *      out_row_stride >= n_out.  Overwritten; `in` and `out` must not overlap.
+ * The staged kernels need `in` 16-byte aligned and in_row_stride * elem a
+ * multiple of 16 bytes; inputs that are not get a plain-load kernel instead
+ * (same result).  Errors: DD_ERR_ARG (null plan/in/out), DD_ERR_SHAPE (a
+ * stride too small), DD_ERR_UNSUPPORTED, DD_ERR_CUDA (launch failure).
+ */
+dd_status dd_forward(dd_plan_t plan, const void* in, int64_t in_row_stride, const float* w,
+                     void* out, int64_t out_row_stride, void* stream);
+
+/*
+ * dd_forward on HOST buffers: copies `host_in` (and `host_w`) to device
+ * buffers the plan owns, runs the forward kernel and copies the result back
+ * to `host_out`, all on `stream`, then waits for the stream.  Layouts as for
+ * dd_forward.  Page-locked host memory gives full copy bandwidth.  The plan's
+ * staging buffers are allocated on first use and kept until the plan is
+ * destroyed (DD_ERR_NOMEM if they cannot be).  Not safe to call concurrently
+ * on the same plan.
+ */
+dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_t in_row_stride,
+                          const float* host_w, void* host_out, int64_t out_row_stride,
+                          void* stream);
+
+/* ---------------------------------------------------------------- adjoint */
+
+/*
+ * Transpose and weight gradient of the weighted Algorithm 1 (not in the
+ * paper; float32 plans only):
+ *   grad_in[c][u] = w[c] * sum over i with 0 <= u - delay(c,i) < n_out of
+ *                   grad_out[i][u - delay(c,i)]          for 0 <= u < n_in
+ *   grad_w[c]     = sum_i sum_t grad_out[i][t] * in[c][t + delay(c,i)]
+ *
+ * grad_out device float [n_dm][go_row_stride], go_row_stride >= n_out.
+ * w        device float[channels] or NULL (unit weights).
+ * grad_in  device float [channels][gi_row_stride], gi_row_stride >= n_in, or
+ *          NULL to skip; its first n_in entries per row are overwritten.
+ * in       device float [channels][in_row_stride] (needed only for grad_w).
+ * grad_w   device float[channels] or NULL to skip; overwritten.
+ * The weight gradient is reduced deterministically (no float atomics): two
+ * calls with the same inputs give bit-identical results.  It uses a scratch
+ * buffer the plan allocates on first use.
+ * Errors: DD_ERR_UNSUPPORTED on a uint8 plan, DD_ERR_ARG if both outputs are
+ * NULL or grad_w is requested without `in`, DD_ERR_SHAPE, DD_ERR_NOMEM,
+ * DD_ERR_CUDA.
+ */
+dd_status dd_adjoint(dd_plan_t plan, const float* grad_out, int64_t go_row_stride,
+                     const float* w, float* grad_in, int64_t gi_row_stride,
+                     const float* in, int64_t in_row_stride, float* grad_w, void* stream);
+
+/* --------------------------------------------------------------- batching */
+
+/*
+ * Many independent beams (Section 2: each beam is processed independently;
+ * Section 5.1: many beams per device) in one persistent kernel launch.
+ * dd_batch_create copies the n plans' geometry into one device work list of
+ * (beam, DM block, time block) tiles, ordered longest first; the plans must
+ * outlive the batch and live on the same device.  Mixed uint8 and float32
+ * plans are allowed.
+ * dd_batch_run: ins[b] / outs[b] are device pointers for beam b with row
+ * strides in_strides[b] / out_strides[b] (host arrays of n entries); results
+ * are bit-identical to n separate dd_forward calls with the same plans and
+ * NULL weights.  The first run on a stream captures the launch into a CUDA
+ * graph keyed by the pointer set; later runs with the same pointers replay it.
+ */
+dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, int32_t n);
+dd_status dd_batch_run(dd_batch_t batch, const void* const* ins, const int64_t* in_strides,
+                       void* const* outs, const int64_t* out_strides, void* stream);
+dd_status dd_batch_destroy(dd_batch_t batch);
+
+/* -------------------------------------------------------------- streaming */
+
+/*
+ * Real-time streaming for one beam (Section 4.2: one second of data must be
+ * dedispersed in under one second).  The state keeps the last max_delay
+ * input samples of every channel on the device, so a stream of chunks of
+ * `chunk_len` samples is dedispersed without re-sending the overlap.
+ * Chunk k (k = 0, 1, ...) covers input samples [k*N, (k+1)*N), N = chunk_len,
+ * and produces output samples [k*N - max_delay, (k+1)*N - max_delay):
+ * *out_t0 receives k*N - max_delay.  The tail starts zero-filled, so outputs
+ * at negative times include those zeros; every output at time >= 0 equals
+ * dd_forward on the concatenated input.
+ * chunk  device [channels][chunk_len] (element type of the plan), contiguous.
+ * out    device [n_dm][chunk_len] of the plan's output type, contiguous.
+ * The plan's n_out is not used by streaming; the output length is chunk_len.
+ * dd_stream_save / dd_stream_restore copy the state (tail + sample counter)
+ * to / from a host buffer of dd_stream_state_bytes bytes, for checkpointing.
+ */
+dd_status dd_stream_create(dd_stream_t* out, dd_plan_t plan, int64_t chunk_len);
+dd_status dd_stream_push(dd_stream_t st, const void* chunk, void* out, int64_t* out_t0, void* stream);
+dd_status dd_stream_reset(dd_stream_t st);
+dd_status dd_stream_state_bytes(dd_stream_t st, int64_t* bytes);
+dd_status dd_stream_save(dd_stream_t st, void* host_buf, void* stream);
+dd_status dd_stream_restore(dd_stream_t st, const void* host_buf, void* stream);
+dd_status dd_stream_destroy(dd_stream_t st);
+
+/* --------------------------------------------------------------- tuning */
+
+/*
+ * Auto-tuning (Section 2.2, last paragraph; Section 4.1): times every valid
+ * tile configuration of the plan on synthetic data with CUDA events (median of
+ * repeated launches) and selects the fastest, within `budget_s` seconds of
+ * wall time (0 = no limit).  If db_path is not NULL the choice is recorded in
+ * that JSON-lines file (one line per call: device name, plan geometry, dtype,
+ * config name, time) and an existing entry for the same key is reused without
+ * timing.  Allocates and frees its own device buffers; synchronises the
+ * device.  *best_ms (nullable) receives the selected config's median time.
+ */
+dd_status dd_tune(dd_plan_t plan, double budget_s, const char* db_path, double* best_ms);
+
+/* ----------------------------------------------------------------- errors */
+
+/* Static name of a status code. */
+const char* dd_status_string(dd_status s);
+/* Detail of the last failing call on this thread ("" if none).  Valid until
+ * the next failing call on the same thread. */
+const char* dd_last_error(void);
+/* Library version string. */
+const char* dd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBDD_DD_H */

@@ -1,0 +1,156 @@
+// C ABI: errors, forward on device buffers and on host buffers.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "dd_errors.h"
+#include "dd_internal.h"
+
+namespace dd {
+
+static thread_local std::string g_last_error;
+
+dd_status set_error(dd_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  std::vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+dd_status set_cuda_error(const char* where, cudaError_t e) {
+  if (e == cudaSuccess) e = cudaGetLastError();
+  return set_error(DD_ERR_CUDA, "%s: %s (%s)", where, cudaGetErrorString(e), cudaGetErrorName(e));
+}
+
+void clear_error() { g_last_error.clear(); }
+
+// Validated launch of the selected (or a fallback) forward kernel.
+dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
+                         int64_t out_stride, cudaStream_t stream, int cfg_override) {
+  if (!in || !out) return set_error(DD_ERR_ARG, "dd_forward: in/out is NULL");
+  if (in_stride < p->n_in)
+    return set_error(DD_ERR_SHAPE, "dd_forward: in_row_stride %lld < n_in %lld", (long long)in_stride,
+                     (long long)p->n_in);
+  if (out_stride < p->n_out)
+    return set_error(DD_ERR_SHAPE, "dd_forward: out_row_stride %lld < n_out %lld", (long long)out_stride,
+                     (long long)p->n_out);
+  if (p->dtype == DD_U8_I32 && w)
+    return set_error(DD_ERR_UNSUPPORTED, "dd_forward: uint8 plans take unit weights only (w must be NULL)");
+  const int elem = p->dtype == DD_U8_I32 ? 1 : 4;
+  FwdArgs a{};
+  a.in = in;
+  a.in_stride = in_stride;
+  a.w = w;
+  a.out = out;
+  a.out_stride = out_stride;
+  a.delays = p->d_delays;
+  a.delaysT = p->d_delaysT;
+  a.regwin_desc = p->d_regwin_desc;
+  a.C = p->C;
+  a.n_dm = p->n_dm;
+  a.n_dm_pad = p->n_dm_pad;
+  a.n_out = p->n_out;
+  a.n_in = p->n_in;
+  a.status = p->d_status;
+  int k = cfg_override >= 0 ? cfg_override : p->selected;
+  const TileConfig* cfg = &p->configs[k];
+  // Bulk copies need a 16-byte aligned source and row pitch; otherwise use the
+  // plain-load kernel, which computes the same sums.
+  const bool aligned = ((uintptr_t)in % 16 == 0) && ((in_stride * elem) % 16 == 0);
+  if (cfg->kind != Kind::Naive && !aligned) {
+    for (size_t j = 0; j < p->configs.size(); ++j)
+      if (p->configs[j].kind == Kind::Naive) {
+        cfg = &p->configs[j];
+        break;
+      }
+  }
+  cudaError_t e = launch_forward(*cfg, p->dtype, a, stream);
+  if (e != cudaSuccess) return set_cuda_error("dd_forward: launch", e);
+  return DD_OK;
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" const char* dd_status_string(dd_status s) {
+  switch (s) {
+    case DD_OK: return "DD_OK";
+    case DD_ERR_ARG: return "DD_ERR_ARG";
+    case DD_ERR_SHAPE: return "DD_ERR_SHAPE";
+    case DD_ERR_ALIGN: return "DD_ERR_ALIGN";
+    case DD_ERR_NOMEM: return "DD_ERR_NOMEM";
+    case DD_ERR_CUDA: return "DD_ERR_CUDA";
+    case DD_ERR_UNSUPPORTED: return "DD_ERR_UNSUPPORTED";
+    case DD_ERR_BUDGET: return "DD_ERR_BUDGET";
+    case DD_ERR_STATE: return "DD_ERR_STATE";
+  }
+  return "DD_ERR_UNKNOWN";
+}
+
+extern "C" const char* dd_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char* dd_version(void) { return "libdd 0.1 (sm_103a)"; }
+
+extern "C" dd_status dd_forward(dd_plan_t plan, const void* in, int64_t in_row_stride, const float* w, void* out,
+                                int64_t out_row_stride, void* stream) {
+  clear_error();
+  if (!plan) return set_error(DD_ERR_ARG, "dd_forward: plan is NULL");
+  return forward_device(plan, in, in_row_stride, w, out, out_row_stride, static_cast<cudaStream_t>(stream), -1);
+}
+
+extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_t in_row_stride,
+                                     const float* host_w, void* host_out, int64_t out_row_stride, void* stream) {
+  clear_error();
+  if (!plan || !host_in || !host_out) return set_error(DD_ERR_ARG, "dd_forward_host: NULL argument");
+  if (in_row_stride < plan->n_in) return set_error(DD_ERR_SHAPE, "dd_forward_host: in_row_stride < n_in");
+  if (out_row_stride < plan->n_out) return set_error(DD_ERR_SHAPE, "dd_forward_host: out_row_stride < n_out");
+  if (plan->dtype == DD_U8_I32 && host_w)
+    return set_error(DD_ERR_UNSUPPORTED, "dd_forward_host: uint8 plans take unit weights only");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t elem = plan->dtype == DD_U8_I32 ? 1 : 4;
+  // device rows padded to 16 bytes so the staged kernels apply
+  const int64_t dev_in_stride = (plan->n_in * (int64_t)elem + 15) / 16 * 16 / (int64_t)elem;
+  const size_t in_bytes = (size_t)plan->C * dev_in_stride * elem;
+  const size_t out_bytes = (size_t)plan->n_dm * plan->n_out * 4;
+  if (plan->h_in_bytes < in_bytes) {
+    cudaFree(plan->h_dev_in);
+    plan->h_dev_in = nullptr;
+    plan->h_in_bytes = 0;
+    if (cudaMalloc(&plan->h_dev_in, in_bytes) != cudaSuccess)
+      return set_error(DD_ERR_NOMEM, "dd_forward_host: cannot allocate %zu input bytes", in_bytes);
+    plan->h_in_bytes = in_bytes;
+  }
+  if (plan->h_out_bytes < out_bytes) {
+    cudaFree(plan->h_dev_out);
+    plan->h_dev_out = nullptr;
+    plan->h_out_bytes = 0;
+    if (cudaMalloc(&plan->h_dev_out, out_bytes) != cudaSuccess)
+      return set_error(DD_ERR_NOMEM, "dd_forward_host: cannot allocate %zu output bytes", out_bytes);
+    plan->h_out_bytes = out_bytes;
+  }
+  if (host_w && !plan->h_dev_w) {
+    if (cudaMalloc(&plan->h_dev_w, (size_t)plan->C * sizeof(float)) != cudaSuccess)
+      return set_error(DD_ERR_NOMEM, "dd_forward_host: cannot allocate weights");
+  }
+  cudaError_t e = cudaMemcpy2DAsync(plan->h_dev_in, dev_in_stride * elem, host_in, in_row_stride * elem,
+                                    plan->n_in * elem, plan->C, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && host_w)
+    e = cudaMemcpyAsync(plan->h_dev_w, host_w, plan->C * sizeof(float), cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return set_cuda_error("dd_forward_host: copy in", e);
+  dd_status st = forward_device(plan, plan->h_dev_in, dev_in_stride, host_w ? plan->h_dev_w : nullptr,
+                                plan->h_dev_out, plan->n_out, s, -1);
+  if (st != DD_OK) return st;
+  e = cudaMemcpy2DAsync(host_out, out_row_stride * 4, plan->h_dev_out, plan->n_out * 4, plan->n_out * 4,
+                        plan->n_dm, cudaMemcpyDeviceToHost, s);
+  if (e != cudaSuccess) return set_cuda_error("dd_forward_host: copy out", e);
+  e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return set_cuda_error("dd_forward_host: synchronize", e);
+  return DD_OK;
+}

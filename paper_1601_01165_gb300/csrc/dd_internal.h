@@ -1,0 +1,90 @@
+// Internal declarations shared by the host API and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "dd.h"
+
+namespace dd {
+
+// Forward kernel families.  NAIVE is the paper's "generically tuned" layout
+// (Section 5: one DM per thread, 1-D blocks, no explicit data reuse); STAGED is
+// the 2-D (DM x time) block of Section 2.2 with each channel's input span
+// staged in shared memory by bulk copies; REGWIN adds reuse in registers across
+// a warp's group of DM trials.
+enum class Kind : int { Naive = 0, Staged = 1, RegWin = 2 };
+
+struct TileConfig {
+  Kind kind;
+  int bd;       // DM trials per block
+  int bt;       // output samples per block
+  int cc;       // channels per pipeline stage
+  int stages;   // pipeline depth
+  int threads;  // threads per block
+  int spl;      // REGWIN: samples per lane
+  int smem;     // dynamic shared memory bytes (filled per plan)
+  int pitch;    // staged row pitch in elements (filled per plan)
+  std::string name;
+};
+
+// Arguments every forward launcher receives (device pointers).
+struct FwdArgs {
+  const void* in;
+  int64_t in_stride;
+  const float* w;
+  void* out;
+  int64_t out_stride;
+  const int32_t* delays;   // [n_dm][C]
+  const int32_t* delaysT;  // [C][n_dm_pad], DMs >= n_dm repeat the last trial
+  const int4* regwin_desc; // REGWIN descriptors [C][n_groups] (may be null)
+  int32_t C;
+  int32_t n_dm;
+  int32_t n_dm_pad;
+  int64_t n_out;
+  int64_t n_in;
+  int* status;             // device error word
+};
+
+// Forward launch on a given configuration.
+cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
+
+// The built-in configuration menu for a dtype (geometry-independent part).
+std::vector<TileConfig> config_menu(dd_dtype dtype);
+
+// Shared-memory limit for one block (opt-in maximum on sm_103a).
+constexpr int kMaxSmemPerBlock = 227 * 1024;
+
+// REGWIN constants: DM trials per warp group and the largest in-group offset
+// the descriptors can carry.
+constexpr int kRwGroup = 8;
+constexpr int kRwMaxOff = 31;
+
+}  // namespace dd
+
+struct dd_plan_s {
+  int device = 0;
+  int32_t C = 0, n_dm = 0, n_dm_pad = 0;
+  int64_t n_out = 0, n_in = 0;
+  int32_t max_delay = 0;
+  double f_low = 0, chan_bw = 0, t_samp = 0, dm_first = 0, dm_step = 0;
+  dd_dtype dtype = DD_F32_F32;
+  std::vector<int32_t> delays;        // host copy [n_dm][C]
+  int32_t* d_delays = nullptr;        // [n_dm][C]
+  int32_t* d_delaysT = nullptr;       // [C][n_dm_pad]
+  int4* d_regwin_desc = nullptr;      // [C][n_groups]
+  int* d_status = nullptr;            // device error word
+  int64_t device_bytes = 0;
+  std::vector<dd::TileConfig> configs;
+  int selected = 0;
+  // host-buffer forward staging (allocated on first dd_forward_host)
+  void* h_dev_in = nullptr;
+  void* h_dev_out = nullptr;
+  float* h_dev_w = nullptr;
+  size_t h_in_bytes = 0, h_out_bytes = 0;
+  // adjoint scratch: per-block partial weight gradients
+  float* wg_partial = nullptr;
+  size_t wg_partial_elems = 0;
+};

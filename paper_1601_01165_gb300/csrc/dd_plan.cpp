@@ -1,0 +1,316 @@
+// Plans: the delay table of Eq. 1 on the host, its device copies, and the
+// per-plan tile configuration menu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "dd_errors.h"
+#include "dd_internal.h"
+
+namespace dd {
+
+std::vector<TileConfig> staged_menu(dd_dtype dtype);
+std::vector<TileConfig> regwin_menu(dd_dtype dtype);
+int staged_smem_for(dd_dtype dtype, int stages, int cc, int bd, int pitch);
+int regwin_smem_for(dd_dtype dtype, const TileConfig& cfg, int pitch);
+
+// Eq. 1 (Section 2): delay in seconds of channel frequency f relative to the
+// top of the band f_h is 4150 * DM * (1/f^2 - 1/f_h^2) (MHz); divided by the
+// sampling time and rounded half up to a whole number of samples.  Evaluated
+// in IEEE double, never in float: float flips entries that lie within 1e-6
+// samples of a rounding boundary.
+static dd_status compute_delay_table(dd_plan_s& p) {
+  const double f_h = p.f_low + (double)(p.C - 1) * p.chan_bw;
+  const double inv_fh2 = 1.0 / (f_h * f_h);
+  p.delays.assign((size_t)p.n_dm * p.C, 0);
+  for (int32_t i = 0; i < p.n_dm; ++i) {
+    const double kdm = 4150.0 * (p.dm_first + (double)i * p.dm_step);
+    for (int32_t c = 0; c < p.C; ++c) {
+      const double f = p.f_low + (double)c * p.chan_bw;
+      const double samples = kdm * (1.0 / (f * f) - inv_fh2) / p.t_samp;
+      const double r = std::floor(samples + 0.5);
+      if (!(r >= 0.0) || r > 2147483647.0)
+        return set_error(DD_ERR_ARG, "delay of channel %d at DM trial %d does not fit int32 (%.3g samples)", c,
+                         i, samples);
+      p.delays[(size_t)i * p.C + c] = (int32_t)r;
+    }
+  }
+  return DD_OK;
+}
+
+// Largest (delay(c, i + bd - 1) - delay(c, i)) over channels and block starts i
+// that are multiples of bd: the widest extra span a block of bd DM trials
+// needs beyond its bt samples.  Trials past n_dm repeat the last one.
+static int32_t block_spread(const dd_plan_s& p, int bd) {
+  int32_t best = 0;
+  for (int32_t i0 = 0; i0 < p.n_dm; i0 += bd) {
+    const int32_t il = std::min(i0 + bd - 1, p.n_dm - 1);
+    for (int32_t c = 0; c < p.C; ++c) {
+      const int32_t s = p.delays[(size_t)il * p.C + c] - p.delays[(size_t)i0 * p.C + c];
+      best = std::max(best, s);
+    }
+  }
+  return best;
+}
+
+// REGWIN descriptor of (channel c, group of kRwGroup trials starting at g*kRwGroup):
+// x = delay of the group's first trial, y/z = offsets of trials 0..3 / 4..7
+// relative to it (one byte each), w = the largest offset.  Returns the largest
+// offset seen (trials past n_dm repeat the last one).
+static int32_t build_regwin_desc(const dd_plan_s& p, std::vector<int4>& desc, int32_t n_groups) {
+  desc.assign((size_t)p.C * n_groups, int4{0, 0, 0, 0});
+  int32_t worst = 0;
+  for (int32_t c = 0; c < p.C; ++c) {
+    for (int32_t g = 0; g < n_groups; ++g) {
+      const int32_t i0 = std::min(g * kRwGroup, p.n_dm - 1);
+      const int32_t base = p.delays[(size_t)i0 * p.C + c];
+      uint32_t packed[2] = {0, 0};
+      int32_t mx = 0;
+      for (int j = 0; j < kRwGroup; ++j) {
+        const int32_t i = std::min(g * kRwGroup + j, p.n_dm - 1);
+        const int32_t o = p.delays[(size_t)i * p.C + c] - base;
+        mx = std::max(mx, o);
+        const uint32_t ob = (uint32_t)std::min(o, 255);
+        packed[j / 4] |= ob << (8 * (j % 4));
+      }
+      worst = std::max(worst, mx);
+      desc[(size_t)c * n_groups + g] = int4{base, (int)packed[0], (int)packed[1], mx};
+    }
+  }
+  return worst;
+}
+
+static void free_plan_device(dd_plan_s* p) {
+  cudaFree(p->d_delays);
+  cudaFree(p->d_delaysT);
+  cudaFree(p->d_regwin_desc);
+  cudaFree(p->d_status);
+  cudaFree(p->h_dev_in);
+  cudaFree(p->h_dev_out);
+  cudaFree(p->h_dev_w);
+  cudaFree(p->wg_partial);
+  p->d_delays = p->d_delaysT = nullptr;
+  p->d_regwin_desc = nullptr;
+  p->d_status = nullptr;
+  p->h_dev_in = p->h_dev_out = nullptr;
+  p->h_dev_w = nullptr;
+  p->wg_partial = nullptr;
+}
+
+// Default configuration: the first valid entry of a preference list chosen by
+// the shape of the problem; dd_tune replaces it with a measured choice.
+static int default_config(const dd_plan_s& p) {
+  const char* prefs_f32[] = {"regwin_f32_w4x2_s15_c8", "staged_d16_t512_c8_s3", "staged_d8_t512_c8_s3",
+                             "staged_d8_t1024_c4_s3", "naive_t256"};
+  const char* prefs_u8[] = {"regwin_u8_w4x2_s16_c8", "staged_d16_t512_c8_s3", "staged_d8_t512_c8_s3",
+                            "staged_d8_t1024_c4_s3", "naive_t256"};
+  const char** prefs = p.dtype == DD_U8_I32 ? prefs_u8 : prefs_f32;
+  for (int k = 0; k < 5; ++k)
+    for (size_t j = 0; j < p.configs.size(); ++j)
+      if (p.configs[j].name == prefs[k]) return (int)j;
+  return 0;
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+static dd_status check_plan_args(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                                 double dm_first, double dm_step, int32_t n_dm) {
+  if (channels <= 0) return set_error(DD_ERR_ARG, "channels must be > 0 (got %d)", channels);
+  if (!(f_low_mhz > 0.0) || !std::isfinite(f_low_mhz)) return set_error(DD_ERR_ARG, "f_low must be > 0 MHz");
+  if (!(chan_bw_mhz > 0.0) || !std::isfinite(chan_bw_mhz)) return set_error(DD_ERR_ARG, "chan_bw must be > 0 MHz");
+  if (!(t_samp_s > 0.0) || !std::isfinite(t_samp_s)) return set_error(DD_ERR_ARG, "t_samp must be > 0 s");
+  if (!(dm_first >= 0.0) || !std::isfinite(dm_first)) return set_error(DD_ERR_ARG, "dm_first must be >= 0");
+  if (!(dm_step >= 0.0) || !std::isfinite(dm_step)) return set_error(DD_ERR_ARG, "dm_step must be >= 0");
+  if (n_dm <= 0) return set_error(DD_ERR_ARG, "n_dm must be > 0 (got %d)", n_dm);
+  if ((int64_t)channels * n_dm > (int64_t)1 << 31)
+    return set_error(DD_ERR_ARG, "delay table of %lld entries is too large", (long long)channels * n_dm);
+  return DD_OK;
+}
+
+extern "C" dd_status dd_delay_table(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                                    double dm_first, double dm_step, int32_t n_dm, int32_t* host_out) {
+  clear_error();
+  if (!host_out) return set_error(DD_ERR_ARG, "dd_delay_table: host_out is NULL");
+  dd_status st = check_plan_args(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm);
+  if (st != DD_OK) return st;
+  dd_plan_s p;
+  p.C = channels;
+  p.n_dm = n_dm;
+  p.f_low = f_low_mhz;
+  p.chan_bw = chan_bw_mhz;
+  p.t_samp = t_samp_s;
+  p.dm_first = dm_first;
+  p.dm_step = dm_step;
+  st = compute_delay_table(p);
+  if (st != DD_OK) return st;
+  std::memcpy(host_out, p.delays.data(), p.delays.size() * sizeof(int32_t));
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan(dd_plan_t* out, int32_t channels, double f_low_mhz, double chan_bw_mhz,
+                             double t_samp_s, double dm_first, double dm_step, int32_t n_dm, int64_t n_out,
+                             dd_dtype dtype) {
+  clear_error();
+  if (!out) return set_error(DD_ERR_ARG, "dd_plan: out is NULL");
+  dd_status chk = check_plan_args(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm);
+  if (chk != DD_OK) return chk;
+  if (n_out <= 0) return set_error(DD_ERR_ARG, "dd_plan: n_out must be > 0");
+  if (dtype != DD_U8_I32 && dtype != DD_F32_F32) return set_error(DD_ERR_ARG, "dd_plan: unknown dtype %d", (int)dtype);
+  if (dtype == DD_U8_I32 && (int64_t)channels * 255 > 2147483647LL)
+    return set_error(DD_ERR_ARG, "dd_plan: %d channels of uint8 overflow int32 sums", channels);
+
+  dd_plan_s* p = new (std::nothrow) dd_plan_s();
+  if (!p) return set_error(DD_ERR_NOMEM, "dd_plan: host allocation failed");
+  p->C = channels;
+  p->n_dm = n_dm;
+  p->n_out = n_out;
+  p->f_low = f_low_mhz;
+  p->chan_bw = chan_bw_mhz;
+  p->t_samp = t_samp_s;
+  p->dm_first = dm_first;
+  p->dm_step = dm_step;
+  p->dtype = dtype;
+  dd_status st = compute_delay_table(*p);
+  if (st != DD_OK) {
+    delete p;
+    return st;
+  }
+  p->max_delay = *std::max_element(p->delays.begin(), p->delays.end());
+  p->n_in = n_out + p->max_delay;
+  p->n_dm_pad = (n_dm + 63) / 64 * 64;
+
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return set_cuda_error("dd_plan: cudaGetDevice");
+  }
+  // transposed, padded copy: [C][n_dm_pad], trials past n_dm repeat the last
+  std::vector<int32_t> dT((size_t)p->C * p->n_dm_pad);
+  for (int32_t c = 0; c < p->C; ++c)
+    for (int32_t i = 0; i < p->n_dm_pad; ++i)
+      dT[(size_t)c * p->n_dm_pad + i] = p->delays[(size_t)std::min(i, n_dm - 1) * p->C + c];
+  const int32_t n_groups = p->n_dm_pad / kRwGroup;
+  std::vector<int4> desc;
+  const int32_t rw_worst = build_regwin_desc(*p, desc, n_groups);
+
+  const size_t bytes_d = p->delays.size() * 4, bytes_dT = dT.size() * 4, bytes_desc = desc.size() * sizeof(int4);
+  cudaError_t e = cudaMalloc(&p->d_delays, bytes_d);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_delaysT, bytes_dT);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_regwin_desc, bytes_desc);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_delays, p->delays.data(), bytes_d, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_delaysT, dT.data(), bytes_dT, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_regwin_desc, desc.data(), bytes_desc, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_plan_device(p);
+    delete p;
+    return e == cudaErrorMemoryAllocation ? set_error(DD_ERR_NOMEM, "dd_plan: device allocation failed")
+                                          : set_cuda_error("dd_plan: upload", e);
+  }
+  p->device_bytes = (int64_t)(bytes_d + bytes_dT + bytes_desc + sizeof(int));
+
+  // configuration menu, filtered by what this geometry allows
+  const int V = p->dtype == DD_U8_I32 ? 16 : 4;
+  for (TileConfig cfg : staged_menu(dtype)) {
+    if (cfg.kind == Kind::Staged) {
+      const int64_t spread = block_spread(*p, cfg.bd);
+      const int64_t pitch = (cfg.bt + spread + 2 * V + V - 1) / V * V;
+      if (pitch > (int64_t)1 << 20) continue;
+      cfg.pitch = (int)pitch;
+      cfg.smem = staged_smem_for(dtype, cfg.stages, cfg.cc, cfg.bd, cfg.pitch);
+      if (cfg.smem > kMaxSmemPerBlock) continue;
+      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
+    }
+    p->configs.push_back(cfg);
+  }
+  if (rw_worst <= kRwMaxOff) {
+    for (TileConfig cfg : regwin_menu(dtype)) {
+      const int64_t spread = block_spread(*p, cfg.bd);
+      const int64_t pitch = (cfg.bt + spread + 2 * V + V - 1) / V * V + (p->dtype == DD_U8_I32 ? 0 : 0);
+      cfg.pitch = (int)pitch;
+      cfg.smem = regwin_smem_for(dtype, cfg, cfg.pitch);
+      if (cfg.smem > kMaxSmemPerBlock) continue;
+      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
+      p->configs.push_back(cfg);
+    }
+  }
+  p->selected = default_config(*p);
+  *out = p;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_destroy(dd_plan_t plan) {
+  clear_error();
+  if (!plan) return DD_OK;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != plan->device) cudaSetDevice(plan->device);
+  free_plan_device(plan);
+  if (prev >= 0 && prev != plan->device) cudaSetDevice(prev);
+  delete plan;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_info(dd_plan_t plan, int64_t* n_in, int32_t* max_delay, int64_t* device_bytes) {
+  clear_error();
+  if (!plan) return set_error(DD_ERR_ARG, "dd_plan_info: plan is NULL");
+  if (n_in) *n_in = plan->n_in;
+  if (max_delay) *max_delay = plan->max_delay;
+  if (device_bytes) *device_bytes = plan->device_bytes;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_delays(dd_plan_t plan, int32_t* host_out) {
+  clear_error();
+  if (!plan || !host_out) return set_error(DD_ERR_ARG, "dd_plan_delays: NULL argument");
+  std::memcpy(host_out, plan->delays.data(), plan->delays.size() * sizeof(int32_t));
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_num_configs(dd_plan_t plan, int32_t* n) {
+  clear_error();
+  if (!plan || !n) return set_error(DD_ERR_ARG, "dd_plan_num_configs: NULL argument");
+  *n = (int32_t)plan->configs.size();
+  return DD_OK;
+}
+
+extern "C" const char* dd_plan_config_name(dd_plan_t plan, int32_t k) {
+  if (!plan || k < 0 || k >= (int32_t)plan->configs.size()) return nullptr;
+  return plan->configs[k].name.c_str();
+}
+
+extern "C" dd_status dd_plan_select_config(dd_plan_t plan, int32_t k) {
+  clear_error();
+  if (!plan) return set_error(DD_ERR_ARG, "dd_plan_select_config: plan is NULL");
+  if (k < 0 || k >= (int32_t)plan->configs.size())
+    return set_error(DD_ERR_ARG, "dd_plan_select_config: config %d out of range [0, %zu)", k, plan->configs.size());
+  plan->selected = k;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_selected_config(dd_plan_t plan, int32_t* k) {
+  clear_error();
+  if (!plan || !k) return set_error(DD_ERR_ARG, "dd_plan_selected_config: NULL argument");
+  *k = plan->selected;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_device_status(dd_plan_t plan, int32_t* code) {
+  clear_error();
+  if (!plan || !code) return set_error(DD_ERR_ARG, "dd_plan_device_status: NULL argument");
+  int v = 0;
+  cudaError_t e = cudaMemcpy(&v, plan->d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return set_cuda_error("dd_plan_device_status", e);
+  *code = v;
+  if (v != 0) {
+    cudaMemset(plan->d_status, 0, sizeof(int));
+    return set_error(DD_ERR_STATE, "a kernel of this plan reported device error %d (1 = bounded wait expired)", v);
+  }
+  return DD_OK;
+}

@@ -1,0 +1,164 @@
+"""GPU parity of the forward path (Algorithm 1) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from paper_1601_01165_gb300 import synth
+from helpers import assert_parity, make_input, oracle_table, oracle_window
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1601_01165_gb300 import binding
+    binding.load()
+    return binding
+
+
+def _run(dd, setup, dtype, seed=0, weighted=False, cfg=None, pulses=0, row_pad=0):
+    plan = dd.Plan.from_setup(setup, dtype)
+    d = oracle_table(setup)
+    assert plan.n_in == setup.n_out + int(d.max())
+    if cfg is not None:
+        plan.select(cfg)
+    stride = plan.padded_in_stride() + row_pad
+    x, sites = make_input(setup, dtype, seed, plan.n_in, stride, pulses, d)
+    w = synth.weights(seed, setup.channels) if weighted else None
+    xt = torch.from_numpy(x).cuda()
+    wt = torch.from_numpy(w).cuda() if w is not None else None
+    out = plan.forward(xt, wt)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    return plan, d, x, w, out.cpu().numpy(), sites
+
+
+def test_plan_delay_table_matches_oracle(dd):
+    for s in (synth.TINY, synth.APERTIF, synth.LOFAR):
+        plan = dd.Plan.from_setup(s, "f32")
+        assert (plan.delays() == oracle_table(s)).all()
+
+
+def _all_configs(dd, setup, dtype):
+    return dd.Plan.from_setup(setup, dtype).configs()
+
+
+@pytest.mark.parametrize("dtype,weighted", [("f32", False), ("f32", True), ("u8", False)])
+def test_tiny_every_config(dd, dtype, weighted):
+    s = synth.TINY
+    for cfg in _all_configs(dd, s, dtype):
+        plan, d, x, w, got, _ = _run(dd, s, dtype, seed=1, weighted=weighted, cfg=cfg)
+        ref, scale = oracle_window(d, x, dtype, 0, s.n_dm, 0, s.n_out, w)
+        assert_parity(got, ref, scale, dtype, where=f"tiny {dtype} w={weighted} {cfg}")
+
+
+RAGGED = [
+    synth.Setup("ragged-a", 37, 1420.0, 0.29296875 * 1024 / 37, 50e-6, 0.0, 0.25, 3, 1001),
+    synth.Setup("ragged-b", 5, 400.0, 8.0, 1e-3, 0.0, 3.0, 1, 17),
+    synth.Setup("ragged-c", 130, 1420.0, 2.0, 50e-6, 0.0, 0.5, 45, 2999),
+    synth.Setup("zero-dm", 64, 1400.0, 1.0, 1e-3, 0.0, 0.0, 2, 1500),
+    synth.Setup("lofar-cut", 32, 138.0, 0.1953125, 5e-6, 0.0, 0.01, 70, 3001),
+    synth.Setup("apertif-cut", 1024, 1420.0, 0.29296875, 50e-6, 3.0, 0.25, 41, 1931),
+]
+
+
+@pytest.mark.parametrize("setup", RAGGED, ids=lambda s: s.name)
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_ragged_every_config(dd, setup, dtype):
+    for cfg in _all_configs(dd, setup, dtype):
+        plan, d, x, w, got, _ = _run(dd, setup, dtype, seed=2, weighted=(dtype == "f32"), cfg=cfg)
+        ref, scale = oracle_window(d, x, dtype, 0, setup.n_dm, 0, setup.n_out, w)
+        assert_parity(got, ref, scale, dtype, where=f"{setup.name} {dtype} {cfg}")
+
+
+def _sample_windows(setup, bd=64, bt=960):
+    """DM row ranges and time windows that straddle tile edges and the ragged tail."""
+    rows = [(0, 20), (bd - 9, bd + 9), (setup.n_dm // 2 - 5, setup.n_dm // 2 + 11), (setup.n_dm - 13, setup.n_dm)]
+    times = [(0, 300), (bt - 150, 300), (setup.n_out // 2, 257), (setup.n_out - 333, 333)]
+    return rows, times
+
+
+@pytest.mark.parametrize("setup,dtype", [(synth.APERTIF, "f32"), (synth.APERTIF, "u8"), (synth.LOFAR, "f32")],
+                         ids=["apertif-f32", "apertif-u8", "lofar-f32"])
+def test_full_size_sampled(dd, setup, dtype):
+    """Full-size configs in the default launch configuration, checked on sampled windows,
+    plus the injected pulses peaking at their true (DM, time) in the GPU output."""
+    plan, d, x, w, got, sites = _run(dd, setup, dtype, seed=0, pulses=3 if setup is synth.APERTIF else 2)
+    rows, times = _sample_windows(setup)
+    for (i0, i1) in rows:
+        for (t0, n_w) in times:
+            ref, scale = oracle_window(d, x, dtype, i0, i1, t0, n_w)
+            assert_parity(got[i0:i1, t0:t0 + n_w], ref, scale, dtype, where=f"{setup.name} rows {i0}:{i1} t {t0}")
+    for (i_p, t_p) in sites:
+        i0, i1 = max(0, i_p - 12), min(setup.n_dm, i_p + 13)
+        ta, tb = max(0, t_p - 40), min(setup.n_out, t_p + 43)
+        ref, scale = oracle_window(d, x, dtype, i0, i1, ta, tb - ta)
+        assert_parity(got[i0:i1, ta:tb], ref, scale, dtype, where=f"pulse window {i_p},{t_p}")
+        blk = got[i0:i1, ta:tb].astype(np.float64)
+        i, t = np.unravel_index(blk.argmax(), blk.shape)
+        assert i0 + i == i_p and t_p <= ta + t <= t_p + 2, (i_p, t_p, i0 + i, ta + t)
+
+
+def test_strides_and_canary(dd):
+    s = synth.Setup("stride", 96, 1420.0, 1.5, 50e-6, 0.0, 0.25, 24, 1234)
+    for dtype in ("f32", "u8"):
+        plan = dd.Plan.from_setup(s, dtype)
+        d = oracle_table(s)
+        stride = plan.padded_in_stride() + (64 if dtype == "u8" else 12)
+        x, _ = make_input(s, dtype, 5, plan.n_in, stride)
+        xt = torch.from_numpy(x).cuda()
+        big = torch.full((s.n_dm, s.n_out + 77), -7, dtype=plan.out_dtype, device="cuda")
+        out = big[:, 5:5 + s.n_out]
+        plan.forward(xt, out=out)
+        torch.cuda.synchronize()
+        b = big.cpu().numpy()
+        assert (b[:, :5] == -7).all() and (b[:, 5 + s.n_out:] == -7).all()
+        ref, scale = oracle_window(d, x, dtype, 0, s.n_dm, 0, s.n_out)
+        assert_parity(b[:, 5:5 + s.n_out], ref, scale, dtype, where=f"strided {dtype}")
+
+
+def test_unaligned_input_uses_plain_kernel(dd):
+    s = synth.Setup("unaligned", 40, 1420.0, 2.0, 50e-6, 0.0, 0.25, 16, 999)
+    plan = dd.Plan.from_setup(s, "f32")
+    d = oracle_table(s)
+    x, _ = make_input(s, "f32", 6, plan.n_in + 1, plan.n_in + 1)
+    xt = torch.from_numpy(x).cuda()
+    view = xt[:, 1:]          # 4-byte offset: not 16-byte aligned
+    out = plan.forward(view)
+    torch.cuda.synchronize()
+    ref, scale = oracle_window(d, np.ascontiguousarray(x[:, 1:]), "f32", 0, s.n_dm, 0, s.n_out)
+    assert_parity(out.cpu().numpy(), ref, scale, "f32", where="unaligned")
+
+
+def test_forward_host_matches_device(dd):
+    s = synth.Setup("host", 256, 1420.0, 1.171875, 50e-6, 0.0, 0.25, 64, 4000)
+    for dtype in ("f32", "u8"):
+        plan = dd.Plan.from_setup(s, dtype)
+        d = oracle_table(s)
+        x, _ = make_input(s, dtype, 7, plan.n_in)
+        xh = torch.from_numpy(x).pin_memory()
+        got = plan.forward_host(xh).numpy()
+        dev = plan.forward(torch.from_numpy(np.ascontiguousarray(
+            np.pad(x, ((0, 0), (0, plan.padded_in_stride() - plan.n_in))))).cuda()).cpu().numpy()
+        assert (got == dev).all()
+        ref, scale = oracle_window(d, x, dtype, 0, s.n_dm, 0, s.n_out)
+        assert_parity(got, ref, scale, dtype, where=f"host {dtype}")
+
+
+def test_errors(dd):
+    s = synth.TINY
+    plan = dd.Plan.from_setup(s, "u8")
+    x = plan.alloc_input()
+    w = torch.ones(s.channels, device="cuda")
+    with pytest.raises(dd.DDError) as e:
+        plan.forward(x, w)
+    assert e.value.name == "DD_ERR_UNSUPPORTED"
+    short = torch.zeros((s.channels, plan.n_in - 1), dtype=torch.uint8, device="cuda")
+    with pytest.raises(dd.DDError) as e:
+        plan.forward(short)
+    assert e.value.name == "DD_ERR_SHAPE"
+    with pytest.raises(dd.DDError) as e:
+        dd.Plan(0, 1400.0, 1.0, 1e-3, 0.0, 1.0, 4, 100)
+    assert e.value.name == "DD_ERR_ARG"
