@@ -52,6 +52,7 @@ dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const 
   a.delays = p->d_delays;
   a.delaysT = p->d_delaysT;
   a.regwin_desc = p->d_regwin_desc;
+  a.quad_desc = p->d_quad_desc;
   a.C = p->C;
   a.n_dm = p->n_dm;
   a.n_dm_pad = p->n_dm_pad;

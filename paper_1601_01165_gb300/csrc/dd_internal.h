@@ -14,8 +14,9 @@ namespace dd {
 // (Section 5: one DM per thread, 1-D blocks, no explicit data reuse); STAGED is
 // the 2-D (DM x time) block of Section 2.2 with each channel's input span
 // staged in shared memory by bulk copies; REGWIN adds reuse in registers across
-// a warp's group of DM trials.
-enum class Kind : int { Naive = 0, Staged = 1, RegWin = 2 };
+// a warp's group of DM trials; TMRW does that reuse through Tensor Memory;
+// U8PK is the uint8 path with packed 16-bit integer sums.
+enum class Kind : int { Naive = 0, Staged = 1, RegWin = 2, TmRw = 3, U8Pk = 4 };
 
 struct TileConfig {
   Kind kind;
@@ -24,7 +25,7 @@ struct TileConfig {
   int cc;       // channels per pipeline stage
   int stages;   // pipeline depth
   int threads;  // threads per block
-  int spl;      // REGWIN: samples per lane
+  int spl;      // REGWIN / TMRW: samples per lane
   int smem;     // dynamic shared memory bytes (filled per plan)
   int pitch;    // staged row pitch in elements (filled per plan)
   std::string name;
@@ -39,7 +40,8 @@ struct FwdArgs {
   int64_t out_stride;
   const int32_t* delays;   // [n_dm][C]
   const int32_t* delaysT;  // [C][n_dm_pad], DMs >= n_dm repeat the last trial
-  const int4* regwin_desc; // REGWIN descriptors [C][n_groups] (may be null)
+  const int4* regwin_desc; // 8-trial group descriptors [C][n_dm_pad / 8]
+  const int4* quad_desc;   // 4-trial group descriptors [C][n_dm_pad / 4]
   int32_t C;
   int32_t n_dm;
   int32_t n_dm_pad;
@@ -74,7 +76,8 @@ struct dd_plan_s {
   std::vector<int32_t> delays;        // host copy [n_dm][C]
   int32_t* d_delays = nullptr;        // [n_dm][C]
   int32_t* d_delaysT = nullptr;       // [C][n_dm_pad]
-  int4* d_regwin_desc = nullptr;      // [C][n_groups]
+  int4* d_regwin_desc = nullptr;      // [C][n_dm_pad / 8]
+  int4* d_quad_desc = nullptr;        // [C][n_dm_pad / 4]
   int* d_status = nullptr;            // device error word
   int64_t device_bytes = 0;
   std::vector<dd::TileConfig> configs;

@@ -187,6 +187,191 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
   }
 }
 
+// ------------------------------------------------------------------- U8PK
+// uint8 -> int32 with packed 16-bit accumulation.  The block stages byte spans
+// exactly like STAGED.  A warp owns DPW DM trials x 32 lanes x 28 samples (7
+// words; odd, so the lanes' word loads hit distinct banks).  Per channel and
+// trial a lane loads 8 words covering its 28 samples at the trial's delay,
+// aligns them with one byte permute whose selector is the same for the whole
+// warp (the delay modulo 4), splits each aligned word into its even and odd
+// samples as 16-bit lanes, and adds two channels at a time into packed 16-bit
+// sums (one 3-input integer add per 4 samples and 2 channels).  256 channels
+// of 8-bit samples fit a 16-bit lane exactly (256 * 255 < 65536), so every
+// 256 channels the packed sums are added into int32 totals and cleared: the
+// result is the exact integer sum.
+template <int WD, int WT, int DPW, int CC, int STAGES>
+__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int pitch) {
+  constexpr int V = 16;
+  constexpr int NW = WD * WT;
+  constexpr int KW = 7;               // words per lane
+  constexpr int SPL = 4 * KW;         // samples per lane
+  constexpr int BD = WD * DPW;
+  constexpr int BT = 32 * SPL * WT;
+  static_assert(BD % 4 == 0 && BT % 16 == 0, "tile shape");
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint8_t* sin = smem_raw;
+  int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + (size_t)STAGES * CC * pitch);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sdel + STAGES * CC * BD);
+
+  const uint8_t* __restrict__ in = static_cast<const uint8_t*>(a.in);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int wd = warp % WD, wt = warp / WD;
+  const int64_t t0 = (int64_t)blockIdx.x * BT;
+  const int i0 = blockIdx.y * BD;
+  const int nt = (int)min((int64_t)BT, a.n_out - t0);
+  const int nchunks = (a.C + CC - 1) / CC;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+
+  auto issue = [&](int k) {
+    const int s = k % STAGES;
+    const int c0 = k * CC;
+    const int cn = min(CC, a.C - c0);
+    auto span = [&](int64_t c, int64_t& al, int64_t& ah) {
+      const int64_t lo = t0 + __ldg(a.delaysT + c * a.n_dm_pad + i0);
+      const int64_t hi = t0 + nt + __ldg(a.delaysT + c * a.n_dm_pad + i0 + BD - 1);
+      al = lo & ~(int64_t)(V - 1);
+      ah = (hi + V - 1) & ~(int64_t)(V - 1);
+    };
+    uint32_t bytes = 0;
+    for (int j = 0; j < cn; ++j) {
+      int64_t al, ah;
+      span(c0 + j, al, ah);
+      bytes += (uint32_t)(ah - al) + BD * 4;
+    }
+    mbar_arrive_expect_tx(&bars[s], bytes);
+    for (int j = 0; j < cn; ++j) {
+      const int64_t c = c0 + j;
+      int64_t al, ah;
+      span(c, al, ah);
+      bulk_g2s(sin + (size_t)(s * CC + j) * pitch, in + c * a.in_stride + al, (uint32_t)(ah - al), &bars[s]);
+      bulk_g2s(sdel + (s * CC + j) * BD, a.delaysT + c * a.n_dm_pad + i0, BD * 4, &bars[s]);
+    }
+  };
+  if (tid == 0) {
+    for (int k = 0; k < min(STAGES, nchunks); ++k) issue(k);
+  }
+
+  uint32_t pe[DPW][KW], po[DPW][KW];  // packed 16-bit sums: even / odd samples of each word
+  int32_t tot[DPW][SPL];
+#pragma unroll
+  for (int m = 0; m < DPW; ++m) {
+#pragma unroll
+    for (int w = 0; w < KW; ++w) pe[m][w] = po[m][w] = 0u;
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) tot[m][q] = 0;
+  }
+  auto flush = [&]() {
+#pragma unroll
+    for (int m = 0; m < DPW; ++m)
+#pragma unroll
+      for (int w = 0; w < KW; ++w) {
+        tot[m][4 * w + 0] += (int32_t)(pe[m][w] & 0xffffu);
+        tot[m][4 * w + 2] += (int32_t)(pe[m][w] >> 16);
+        tot[m][4 * w + 1] += (int32_t)(po[m][w] & 0xffffu);
+        tot[m][4 * w + 3] += (int32_t)(po[m][w] >> 16);
+        pe[m][w] = po[m][w] = 0u;
+      }
+  };
+  // aligned words of (trial slot m, channel row j of stage s) -> x[KW]
+  auto aligned = [&](int s, int j, int m, uint32_t (&x)[KW]) {
+    const uint8_t* row = sin + (size_t)(s * CC + j) * pitch;
+    const int32_t* dl = sdel + (s * CC + j) * BD;
+    const int d0 = dl[0];
+    const int64_t al = (t0 + d0) & ~(int64_t)(V - 1);
+    const int off = (int)(t0 + dl[wd * DPW + m] - al) + wt * 32 * SPL + lane * SPL;
+    const uint32_t* wp = reinterpret_cast<const uint32_t*>(row) + (off >> 2);
+    const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(off & 3);
+    uint32_t wv[KW + 1];
+#pragma unroll
+    for (int w = 0; w <= KW; ++w) wv[w] = wp[w];
+#pragma unroll
+    for (int w = 0; w < KW; ++w) x[w] = __byte_perm(wv[w], wv[w + 1], sel);
+  };
+
+  int since_flush = 0;
+  for (int k = 0; k < nchunks; ++k) {
+    const int s = k % STAGES;
+    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((k / STAGES) & 1), kWaitLimitCycles);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        report_error(a.status, kDevWaitTimeout);
+        for (int kk = k; kk < min(k + STAGES, nchunks); ++kk)
+          (void)mbar_wait_bounded(&bars[kk % STAGES], (uint32_t)((kk / STAGES) & 1), kWaitLimitCycles);
+      }
+      return;
+    }
+    if (tid == 0 && k >= 1 && k - 1 + STAGES < nchunks) issue(k - 1 + STAGES);
+    const int cn = min(CC, a.C - k * CC);
+    int j = 0;
+    for (; j + 1 < cn; j += 2) {
+      if (since_flush >= 255) {  // the next two channels would pass 256
+        flush();
+        since_flush = 0;
+      }
+#pragma unroll
+      for (int m = 0; m < DPW; ++m) {
+        uint32_t x0[KW], x1[KW];
+        aligned(s, j, m, x0);
+        aligned(s, j + 1, m, x1);
+#pragma unroll
+        for (int w = 0; w < KW; ++w) {
+          pe[m][w] += __byte_perm(x0[w], 0u, 0x4240u) + __byte_perm(x1[w], 0u, 0x4240u);
+          po[m][w] += __byte_perm(x0[w], 0u, 0x4341u) + __byte_perm(x1[w], 0u, 0x4341u);
+        }
+      }
+      since_flush += 2;
+    }
+    if (j < cn) {
+      if (since_flush >= 256) {
+        flush();
+        since_flush = 0;
+      }
+#pragma unroll
+      for (int m = 0; m < DPW; ++m) {
+        uint32_t x0[KW];
+        aligned(s, j, m, x0);
+#pragma unroll
+        for (int w = 0; w < KW; ++w) {
+          pe[m][w] += __byte_perm(x0[w], 0u, 0x4240u);
+          po[m][w] += __byte_perm(x0[w], 0u, 0x4341u);
+        }
+      }
+      since_flush += 1;
+    }
+  }
+  flush();
+
+  // transpose through shared memory (stage area is free: every chunk was consumed)
+  __syncthreads();
+  int32_t* epi = reinterpret_cast<int32_t*>(smem_raw) + (size_t)warp * DPW * 32 * SPL;
+#pragma unroll
+  for (int m = 0; m < DPW; ++m)
+#pragma unroll
+    for (int q = 0; q < SPL; ++q) epi[m * 32 * SPL + lane * SPL + q] = tot[m][q];
+  __syncwarp();
+  int32_t* __restrict__ out = static_cast<int32_t*>(a.out);
+  const int tw0 = wt * 32 * SPL;
+  const int lim = min(32 * SPL, nt - tw0);
+  for (int m = 0; m < DPW; ++m) {
+    const int i = i0 + wd * DPW + m;
+    if (i >= a.n_dm) break;
+    int32_t* orow = out + (int64_t)i * a.out_stride + t0 + tw0;
+    for (int u = lane; u < lim; u += 32) orow[u] = epi[m * 32 * SPL + u];
+  }
+}
+
+__host__ __device__ constexpr int u8pk_smem_bytes(int stages, int cc, int bd, int pitch, int nw, int dpw) {
+  return (stages * cc * pitch + stages * cc * bd * 4 + stages * 8) > nw * dpw * 32 * 28 * 4
+             ? (stages * cc * pitch + stages * cc * bd * 4 + stages * 8)
+             : nw * dpw * 32 * 28 * 4;
+}
+
 // --------------------------------------------------------------- dispatch
 
 template <typename Tin, bool WEIGHTED>
@@ -219,6 +404,35 @@ static cudaError_t launch_staged_t(const TileConfig& cfg, const FwdArgs& a, cuda
   X(32, 512, 4, 3)           \
   X(64, 256, 4, 3)
 
+#define DD_U8PK_CASES(X) \
+  X(8, 1, 2, 16, 4)      \
+  X(4, 2, 2, 16, 4)      \
+  X(8, 1, 4, 16, 3)      \
+  X(4, 1, 2, 32, 3)      \
+  X(8, 2, 1, 16, 4)
+
+template <int WD, int WT, int DPW, int CC, int ST>
+static cudaError_t launch_u8pk_t(const TileConfig& cfg, const FwdArgs& a, cudaStream_t s) {
+  auto kern = fwd_u8pk_kernel<WD, WT, DPW, CC, ST>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, cfg.smem);
+  if (e != cudaSuccess) return e;
+  constexpr int BD = WD * DPW, BT = 32 * 28 * WT;
+  dim3 grid((unsigned)((a.n_out + BT - 1) / BT), (unsigned)((a.n_dm + BD - 1) / BD));
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  kern<<<grid, 32 * WD * WT, cfg.smem, s>>>(a, cfg.pitch);
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_u8pk(const TileConfig& cfg, const FwdArgs& a, cudaStream_t s) {
+#define X(WD_, WT_, DPW_, CC_, ST_)                                                                   \
+  if (cfg.bd == WD_ * DPW_ && cfg.bt == 32 * 28 * WT_ && cfg.threads == 32 * WD_ * WT_ && cfg.cc == CC_ && \
+      cfg.stages == ST_)                                                                               \
+    return launch_u8pk_t<WD_, WT_, DPW_, CC_, ST_>(cfg, a, s);
+  DD_U8PK_CASES(X)
+#undef X
+  return cudaErrorInvalidConfiguration;
+}
+
 template <typename Tin, bool WEIGHTED>
 static cudaError_t launch_staged(const TileConfig& cfg, const FwdArgs& a, cudaStream_t s) {
 #define X(BD_, BT_, CC_, ST_)                                                    \
@@ -230,6 +444,7 @@ static cudaError_t launch_staged(const TileConfig& cfg, const FwdArgs& a, cudaSt
 }
 
 cudaError_t launch_regwin(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_tmrw(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
 
 cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s) {
   const bool weighted = a.w != nullptr;
@@ -242,6 +457,11 @@ cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs&
       return weighted ? launch_staged<float, true>(cfg, a, s) : launch_staged<float, false>(cfg, a, s);
     case Kind::RegWin:
       return launch_regwin(cfg, dtype, a, s);
+    case Kind::TmRw:
+      return launch_tmrw(cfg, dtype, a, s);
+    case Kind::U8Pk:
+      if (dtype != DD_U8_I32 || weighted) return cudaErrorInvalidConfiguration;
+      return launch_u8pk(cfg, a, s);
   }
   return cudaErrorInvalidConfiguration;
 }
@@ -257,6 +477,22 @@ std::vector<TileConfig> staged_menu(dd_dtype dtype) {
   DD_STAGED_CASES(X)
 #undef X
   return v;
+}
+
+std::vector<TileConfig> u8pk_menu(dd_dtype dtype) {
+  std::vector<TileConfig> v;
+  if (dtype != DD_U8_I32) return v;
+#define X(WD_, WT_, DPW_, CC_, ST_)                                                                  \
+  v.push_back({Kind::U8Pk, WD_ * DPW_, 32 * 28 * WT_, CC_, ST_, 32 * WD_ * WT_, 28, 0, 0,            \
+               "u8pk_w" #WD_ "x" #WT_ "_d" #DPW_ "_c" #CC_ "_st" #ST_});
+  DD_U8PK_CASES(X)
+#undef X
+  return v;
+}
+
+int u8pk_smem_for(const TileConfig& cfg, int pitch) {
+  const int nw = cfg.threads / 32, wd = nw / (cfg.bt / (32 * 28));
+  return u8pk_smem_bytes(cfg.stages, cfg.cc, cfg.bd, pitch, nw, cfg.bd / wd);
 }
 
 int staged_smem_for(dd_dtype dtype, int stages, int cc, int bd, int pitch) {
