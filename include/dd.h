@@ -188,6 +188,34 @@ dd_status dd_adjoint(dd_plan_t plan, const float* grad_out, int64_t go_row_strid
                      const float* w, float* grad_in, int64_t gi_row_stride,
                      const float* in, int64_t in_row_stride, float* grad_w, void* stream);
 
+/* ------------------------------------------------------------------- loss */
+
+/*
+ * Detection statistic over a dedispersed block (not in the paper; the loss of
+ * the differentiable configuration).  For each row i of x ([n_rows][row_stride]
+ * float, first n_cols used, n_cols >= 8): boxcar b[t] = sum_{k<8} x[i][t+k] for
+ * t in [0, n_cols - 7); mean m_i and population standard deviation s_i of b;
+ * S/N z[i][t] = (b[t] - m_i) / s_i.  The maximum of z over (i, t) -- the first
+ * one on ties, lowest i then lowest t -- and loss = -max are written to
+ * *result (device memory).  Rows with s_i = 0 have no S/N and are skipped;
+ * valid = 0 if all are.  If grad (device, [n_rows][grad_stride]) is not NULL
+ * it receives d loss / d x: nonzero only in the best row.  Sums are taken in
+ * double.  Scratch: n_rows * 32 bytes from the stream-ordered allocator.
+ * Errors: DD_ERR_ARG, DD_ERR_SHAPE (n_cols < 8, strides), DD_ERR_NOMEM, DD_ERR_CUDA.
+ */
+typedef struct {
+  double loss;      /* -max S/N */
+  double snr;       /* max S/N */
+  double mean;      /* boxcar mean of the best row */
+  double std;       /* boxcar population standard deviation of the best row */
+  int64_t best_t;   /* boxcar start of the maximum */
+  int32_t best_row; /* row of the maximum */
+  int32_t valid;    /* 0 if every row is constant */
+} dd_snr_result;
+
+dd_status dd_boxcar_snr(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
+                        dd_snr_result* result, float* grad, int64_t grad_stride, void* stream);
+
 /* --------------------------------------------------------------- batching */
 
 /*

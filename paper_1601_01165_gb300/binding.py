@@ -83,6 +83,7 @@ def _declare(lib):
         "dd_stream_restore": (st, [vp, vp, vp]),
         "dd_stream_destroy": (st, [vp]),
         "dd_tune": (st, [vp, dbl, ctypes.c_char_p, PD]),
+        "dd_boxcar_snr": (st, [vp, i64, i32, i64, vp, vp, i64, vp]),
         "dd_status_string": (ctypes.c_char_p, [st]),
         "dd_last_error": (ctypes.c_char_p, []),
         "dd_version": (ctypes.c_char_p, []),
@@ -249,15 +250,19 @@ class Plan:
                                      _stream_handle(stream)), "dd_forward_host")
         return out
 
-    def adjoint(self, grad_out, w=None, x=None, grad_in=True, grad_w=False, stream=None):
-        """Transpose of the weighted forward (grad_in) and d/dw (grad_w); returns (grad_in, grad_w)."""
+    def adjoint(self, grad_out, w=None, x=None, grad_in=True, grad_w=False, stream=None, grad_in_out=None):
+        """Transpose of the weighted forward (grad_in) and d/dw (grad_w); returns (grad_in, grad_w).
+
+        grad_in_out, if given, is a [C][>= n_in] float32 tensor that receives grad_in
+        (only its first n_in columns are written)."""
         import torch
         go_stride = _rows(grad_out, "grad_out", torch.float32, self.device)
         gi = gw = None
         gi_stride = 0
         if grad_in:
-            gi = torch.empty((self.channels, self.n_in), dtype=torch.float32, device=self.device)
-            gi_stride = gi.stride(0)
+            gi = grad_in_out if grad_in_out is not None else \
+                torch.empty((self.channels, self.n_in), dtype=torch.float32, device=self.device)
+            gi_stride = _rows(gi, "grad_in", torch.float32, self.device)
         in_stride = 0
         if grad_w:
             if x is None:
@@ -276,3 +281,30 @@ class Plan:
         check(load().dd_tune(self._h, float(budget_s), None if db_path is None else db_path.encode(),
                              ctypes.byref(ms)), "dd_tune")
         return self.selected, ms.value
+
+
+SNR_FIELDS = ("loss", "snr", "mean", "std", "best_t", "best_row", "valid")
+
+
+def boxcar_snr(x, grad=False, stream=None):
+    """dd_boxcar_snr: 8-sample boxcar S/N over each row of x ([rows][>= cols] float32 CUDA).
+
+    Returns (result, grad_tensor | None, raw) where `result` is a dict read back
+    from the device (synchronises the stream) and `raw` the 48-byte device
+    buffer (raw.view(torch.float64)[0] is the loss, still on the device)."""
+    import torch
+    stride = _rows(x, "x", torch.float32, x.device)
+    n_rows, n_cols = x.shape
+    raw = torch.zeros(48, dtype=torch.uint8, device=x.device)
+    g = torch.empty_like(x) if grad else None
+    check(load().dd_boxcar_snr(x.data_ptr(), stride, n_rows, n_cols, raw.data_ptr(),
+                               None if g is None else g.data_ptr(), 0 if g is None else g.stride(0),
+                               _stream_handle(stream)), "dd_boxcar_snr")
+    return raw, g
+
+
+def snr_result(raw) -> dict:
+    import struct
+    b = bytes(raw.cpu().numpy().tobytes())
+    vals = struct.unpack("<4dqii", b)
+    return dict(zip(SNR_FIELDS, vals))

@@ -53,8 +53,13 @@ struct FwdArgs {
 // Forward launch on a given configuration.
 cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
 
-// The built-in configuration menu for a dtype (geometry-independent part).
-std::vector<TileConfig> config_menu(dd_dtype dtype);
+// Sizes, device tables and configuration menu of a plan whose host delay
+// table is filled in (dd_plan.cpp).
+dd_status finish_plan(dd_plan_s* p);
+void free_plan_device(dd_plan_s* p);
+// Validated forward launch (dd_api.cpp); cfg_override < 0 uses the plan's choice.
+dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
+                         int64_t out_stride, cudaStream_t stream, int cfg_override);
 
 // Shared-memory limit for one block (opt-in maximum on sm_103a).
 constexpr int kMaxSmemPerBlock = 227 * 1024;
@@ -87,7 +92,11 @@ struct dd_plan_s {
   void* h_dev_out = nullptr;
   float* h_dev_w = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;
-  // adjoint scratch: per-block partial weight gradients
-  float* wg_partial = nullptr;
-  size_t wg_partial_elems = 0;
+  // adjoint: the transposed plan (channels and DM trials swapped, delays
+  // max_delay - delay) and its zero-padded copy of grad_out
+  dd_plan_s* adj = nullptr;
+  float* adj_pad = nullptr;       // [n_dm][adj_pad_stride]
+  int64_t adj_pad_stride = 0;
+  float* adj_g = nullptr;         // [C][adj_g_stride] unweighted transpose when grad_in is not requested
+  int64_t adj_g_stride = 0;
 };

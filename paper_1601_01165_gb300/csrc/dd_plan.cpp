@@ -90,7 +90,7 @@ static int32_t build_group_desc(const dd_plan_s& p, std::vector<int4>& desc, int
   return worst;
 }
 
-static void free_plan_device(dd_plan_s* p) {
+void free_plan_device(dd_plan_s* p) {
   cudaFree(p->d_delays);
   cudaFree(p->d_delaysT);
   cudaFree(p->d_regwin_desc);
@@ -99,14 +99,20 @@ static void free_plan_device(dd_plan_s* p) {
   cudaFree(p->h_dev_in);
   cudaFree(p->h_dev_out);
   cudaFree(p->h_dev_w);
-  cudaFree(p->wg_partial);
+  cudaFree(p->adj_pad);
+  cudaFree(p->adj_g);
+  if (p->adj) {
+    free_plan_device(p->adj);
+    delete p->adj;
+    p->adj = nullptr;
+  }
   p->d_delays = p->d_delaysT = nullptr;
   p->d_regwin_desc = nullptr;
   p->d_quad_desc = nullptr;
   p->d_status = nullptr;
   p->h_dev_in = p->h_dev_out = nullptr;
   p->h_dev_w = nullptr;
-  p->wg_partial = nullptr;
+  p->adj_pad = p->adj_g = nullptr;
 }
 
 // Default configuration: the first valid entry of a preference list chosen by
@@ -122,6 +128,93 @@ static int default_config(const dd_plan_s& p) {
     for (size_t j = 0; j < p.configs.size(); ++j)
       if (p.configs[j].name == prefs[k]) return (int)j;
   return 0;
+}
+
+// Everything a plan derives from its delay table (p->delays [n_dm][C], rows
+// non-decreasing along the trial index for every channel): sizes, device
+// copies of the table and descriptors, and the configuration menu.
+dd_status finish_plan(dd_plan_s* p) {
+  p->max_delay = *std::max_element(p->delays.begin(), p->delays.end());
+  p->n_in = p->n_out + p->max_delay;
+  p->n_dm_pad = (p->n_dm + 63) / 64 * 64;
+
+  if (cudaGetDevice(&p->device) != cudaSuccess) return set_cuda_error("dd_plan: cudaGetDevice");
+  // transposed, padded copy: [C][n_dm_pad], trials past n_dm repeat the last
+  std::vector<int32_t> dT((size_t)p->C * p->n_dm_pad);
+  for (int32_t c = 0; c < p->C; ++c)
+    for (int32_t i = 0; i < p->n_dm_pad; ++i)
+      dT[(size_t)c * p->n_dm_pad + i] = p->delays[(size_t)std::min(i, p->n_dm - 1) * p->C + c];
+  const int32_t n_groups = p->n_dm_pad / kRwGroup;
+  std::vector<int4> desc, desc4;
+  const int32_t rw_worst = build_group_desc(*p, desc, n_groups, kRwGroup);
+  (void)build_group_desc(*p, desc4, p->n_dm_pad / 4, 4);
+
+  const size_t bytes_d = p->delays.size() * 4, bytes_dT = dT.size() * 4, bytes_desc = desc.size() * sizeof(int4);
+  const size_t bytes_desc4 = desc4.size() * sizeof(int4);
+  cudaError_t e = cudaMalloc(&p->d_delays, bytes_d);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_delaysT, bytes_dT);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_regwin_desc, bytes_desc);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_quad_desc, bytes_desc4);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_quad_desc, desc4.data(), bytes_desc4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_delays, p->delays.data(), bytes_d, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_delaysT, dT.data(), bytes_dT, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(p->d_regwin_desc, desc.data(), bytes_desc, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    free_plan_device(p);
+    return e == cudaErrorMemoryAllocation ? set_error(DD_ERR_NOMEM, "dd_plan: device allocation failed")
+                                          : set_cuda_error("dd_plan: upload", e);
+  }
+  p->device_bytes = (int64_t)(bytes_d + bytes_dT + bytes_desc + bytes_desc4 + sizeof(int));
+
+  // configuration menu, filtered by what this geometry allows
+  const int V = p->dtype == DD_U8_I32 ? 16 : 4;
+  for (TileConfig cfg : staged_menu(p->dtype)) {
+    if (cfg.kind == Kind::Staged) {
+      const int64_t spread = block_spread(*p, cfg.bd);
+      const int64_t pitch = (cfg.bt + spread + 2 * V + V - 1) / V * V;
+      if (pitch > (int64_t)1 << 20) continue;
+      cfg.pitch = (int)pitch;
+      cfg.smem = staged_smem_for(p->dtype, cfg.stages, cfg.cc, cfg.bd, cfg.pitch);
+      if (cfg.smem > kMaxSmemPerBlock) continue;
+      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
+    }
+    p->configs.push_back(cfg);
+  }
+  for (TileConfig cfg : u8pk_menu(p->dtype)) {
+    const int64_t spread = block_spread(*p, cfg.bd);
+    // + 32: a lane reads 32 bytes from a word-aligned start at or before its first sample
+    const int64_t pitch = (cfg.bt + spread + 2 * V + 32 + V - 1) / V * V;
+    if (pitch > (int64_t)1 << 20) continue;
+    cfg.pitch = (int)pitch;
+    cfg.smem = u8pk_smem_for(cfg, cfg.pitch);
+    if (cfg.smem > kMaxSmemPerBlock) continue;
+    if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
+    p->configs.push_back(cfg);
+  }
+  if (rw_worst <= kRwMaxOff) {
+    for (TileConfig cfg : regwin_menu(p->dtype)) {
+      const int64_t spread = block_spread(*p, cfg.bd);
+      const int64_t pitch = (cfg.bt + spread + 2 * V + V - 1) / V * V + (p->dtype == DD_U8_I32 ? 0 : 0);
+      cfg.pitch = (int)pitch;
+      cfg.smem = regwin_smem_for(p->dtype, cfg, cfg.pitch);
+      if (cfg.smem > kMaxSmemPerBlock) continue;
+      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
+      p->configs.push_back(cfg);
+    }
+    for (TileConfig cfg : tmrw_menu(p->dtype)) {
+      const int64_t spread = block_spread(*p, cfg.bd);
+      // + 32: window loads run in blocks of 8 and may read past the window
+      cfg.pitch = (int)((cfg.bt + spread + 2 * V + 32 + V - 1) / V * V);
+      cfg.smem = tmrw_smem_for(cfg, cfg.pitch);
+      if (cfg.smem > kMaxSmemPerBlock) continue;
+      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
+      p->configs.push_back(cfg);
+    }
+  }
+  p->selected = default_config(*p);
+  return DD_OK;
 }
 
 }  // namespace dd
@@ -190,90 +283,11 @@ extern "C" dd_status dd_plan(dd_plan_t* out, int32_t channels, double f_low_mhz,
     delete p;
     return st;
   }
-  p->max_delay = *std::max_element(p->delays.begin(), p->delays.end());
-  p->n_in = n_out + p->max_delay;
-  p->n_dm_pad = (n_dm + 63) / 64 * 64;
-
-  if (cudaGetDevice(&p->device) != cudaSuccess) {
+  st = finish_plan(p);
+  if (st != DD_OK) {
     delete p;
-    return set_cuda_error("dd_plan: cudaGetDevice");
+    return st;
   }
-  // transposed, padded copy: [C][n_dm_pad], trials past n_dm repeat the last
-  std::vector<int32_t> dT((size_t)p->C * p->n_dm_pad);
-  for (int32_t c = 0; c < p->C; ++c)
-    for (int32_t i = 0; i < p->n_dm_pad; ++i)
-      dT[(size_t)c * p->n_dm_pad + i] = p->delays[(size_t)std::min(i, n_dm - 1) * p->C + c];
-  const int32_t n_groups = p->n_dm_pad / kRwGroup;
-  std::vector<int4> desc, desc4;
-  const int32_t rw_worst = build_group_desc(*p, desc, n_groups, kRwGroup);
-  (void)build_group_desc(*p, desc4, p->n_dm_pad / 4, 4);
-
-  const size_t bytes_d = p->delays.size() * 4, bytes_dT = dT.size() * 4, bytes_desc = desc.size() * sizeof(int4);
-  const size_t bytes_desc4 = desc4.size() * sizeof(int4);
-  cudaError_t e = cudaMalloc(&p->d_delays, bytes_d);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_delaysT, bytes_dT);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_regwin_desc, bytes_desc);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_quad_desc, bytes_desc4);
-  if (e == cudaSuccess) e = cudaMemcpy(p->d_quad_desc, desc4.data(), bytes_desc4, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
-  if (e == cudaSuccess) e = cudaMemcpy(p->d_delays, p->delays.data(), bytes_d, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(p->d_delaysT, dT.data(), bytes_dT, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(p->d_regwin_desc, desc.data(), bytes_desc, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
-  if (e != cudaSuccess) {
-    free_plan_device(p);
-    delete p;
-    return e == cudaErrorMemoryAllocation ? set_error(DD_ERR_NOMEM, "dd_plan: device allocation failed")
-                                          : set_cuda_error("dd_plan: upload", e);
-  }
-  p->device_bytes = (int64_t)(bytes_d + bytes_dT + bytes_desc + bytes_desc4 + sizeof(int));
-
-  // configuration menu, filtered by what this geometry allows
-  const int V = p->dtype == DD_U8_I32 ? 16 : 4;
-  for (TileConfig cfg : staged_menu(dtype)) {
-    if (cfg.kind == Kind::Staged) {
-      const int64_t spread = block_spread(*p, cfg.bd);
-      const int64_t pitch = (cfg.bt + spread + 2 * V + V - 1) / V * V;
-      if (pitch > (int64_t)1 << 20) continue;
-      cfg.pitch = (int)pitch;
-      cfg.smem = staged_smem_for(dtype, cfg.stages, cfg.cc, cfg.bd, cfg.pitch);
-      if (cfg.smem > kMaxSmemPerBlock) continue;
-      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
-    }
-    p->configs.push_back(cfg);
-  }
-  for (TileConfig cfg : u8pk_menu(dtype)) {
-    const int64_t spread = block_spread(*p, cfg.bd);
-    // + 32: a lane reads 32 bytes from a word-aligned start at or before its first sample
-    const int64_t pitch = (cfg.bt + spread + 2 * V + 32 + V - 1) / V * V;
-    if (pitch > (int64_t)1 << 20) continue;
-    cfg.pitch = (int)pitch;
-    cfg.smem = u8pk_smem_for(cfg, cfg.pitch);
-    if (cfg.smem > kMaxSmemPerBlock) continue;
-    if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
-    p->configs.push_back(cfg);
-  }
-  if (rw_worst <= kRwMaxOff) {
-    for (TileConfig cfg : regwin_menu(dtype)) {
-      const int64_t spread = block_spread(*p, cfg.bd);
-      const int64_t pitch = (cfg.bt + spread + 2 * V + V - 1) / V * V + (p->dtype == DD_U8_I32 ? 0 : 0);
-      cfg.pitch = (int)pitch;
-      cfg.smem = regwin_smem_for(dtype, cfg, cfg.pitch);
-      if (cfg.smem > kMaxSmemPerBlock) continue;
-      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
-      p->configs.push_back(cfg);
-    }
-    for (TileConfig cfg : tmrw_menu(dtype)) {
-      const int64_t spread = block_spread(*p, cfg.bd);
-      // + 32: window loads run in blocks of 8 and may read past the window
-      cfg.pitch = (int)((cfg.bt + spread + 2 * V + 32 + V - 1) / V * V);
-      cfg.smem = tmrw_smem_for(cfg, cfg.pitch);
-      if (cfg.smem > kMaxSmemPerBlock) continue;
-      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
-      p->configs.push_back(cfg);
-    }
-  }
-  p->selected = default_config(*p);
   *out = p;
   return DD_OK;
 }

@@ -1,0 +1,210 @@
+// Boxcar-8 S/N detection loss over a dedispersed block, and its gradient.
+//
+// Not part of the paper: this is the loss of the differentiable
+// configuration (dedisperse -> 8-sample boxcar -> maximum S/N).  Per row i:
+// b[t] = sum_{k<8} x[i][t+k], mean m and population sd s of b over
+// t < nb = n_cols - 7, z[t] = (b[t] - m) / s.  loss = -max_{i,t} z (first on
+// ties).  For the best row i*, t*:
+//   d z[t*] / d b[t] = ((t == t*) - 1/nb) / s - z[t*] z[t] / (nb s)
+//   d loss / d x[i*][u] = -sum over t in [u-7, u] of d z[t*] / d b[t].
+// All sums in double; each row is one block with a fixed reduction tree.
+#include <cuda_runtime.h>
+
+#include <cfloat>
+
+#include "dd_errors.h"
+#include "dd_internal.h"
+
+namespace dd {
+
+constexpr int kBox = 8;
+
+struct RowStat {
+  double z;      // best S/N in the row (-inf if the row is constant)
+  double mean;
+  double sd;
+  int64_t t;     // boxcar start of the best S/N
+};
+
+__device__ __forceinline__ double boxcar(const float* row, int64_t t) {
+  double b = 0.0;
+#pragma unroll
+  for (int k = 0; k < kBox; ++k) b += (double)__ldg(row + t + k);
+  return b;
+}
+
+template <int NT>
+__device__ double block_sum(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+    __syncthreads();
+  }
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+// One block per row: mean, sd, best S/N and where it is.
+template <int NT>
+__global__ void __launch_bounds__(NT) snr_rows_kernel(const float* __restrict__ x, int64_t stride, int64_t n_cols,
+                                                      RowStat* __restrict__ stats) {
+  __shared__ double red[NT];
+  __shared__ double zbest[NT];
+  __shared__ int64_t tbest[NT];
+  const int i = blockIdx.x;
+  const float* row = x + (int64_t)i * stride;
+  const int64_t nb = n_cols - kBox + 1;
+  double s = 0.0;
+  for (int64_t t = threadIdx.x; t < nb; t += NT) s += boxcar(row, t);
+  const double mean = block_sum<NT>(s, red) / (double)nb;
+  double v = 0.0;
+  for (int64_t t = threadIdx.x; t < nb; t += NT) {
+    const double d = boxcar(row, t) - mean;
+    v += d * d;
+  }
+  const double sd = sqrt(block_sum<NT>(v, red) / (double)nb);
+  double zb = -DBL_MAX;
+  int64_t tb = -1;
+  if (sd > 0.0) {
+    for (int64_t t = threadIdx.x; t < nb; t += NT) {
+      const double z = (boxcar(row, t) - mean) / sd;
+      if (z > zb) {  // t increases along the loop, so the first maximum is kept
+        zb = z;
+        tb = t;
+      }
+    }
+  }
+  zbest[threadIdx.x] = zb;
+  tbest[threadIdx.x] = tb;
+  __syncthreads();
+  for (int h = NT / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      const double zo = zbest[threadIdx.x + h];
+      const int64_t to = tbest[threadIdx.x + h];
+      if (zo > zbest[threadIdx.x] || (zo == zbest[threadIdx.x] && to >= 0 && (tbest[threadIdx.x] < 0 || to < tbest[threadIdx.x]))) {
+        zbest[threadIdx.x] = zo;
+        tbest[threadIdx.x] = to;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) stats[i] = RowStat{sd > 0.0 ? zbest[0] : -DBL_MAX, mean, sd, sd > 0.0 ? tbest[0] : -1};
+}
+
+// One block: the best row (first on ties) -> result.
+template <int NT>
+__global__ void __launch_bounds__(NT) snr_pick_kernel(const RowStat* __restrict__ stats, int n_rows,
+                                                      dd_snr_result* __restrict__ result) {
+  __shared__ double zb[NT];
+  __shared__ int ib[NT];
+  double z = -DBL_MAX;
+  int bi = -1;
+  for (int i = threadIdx.x; i < n_rows; i += NT) {
+    if (stats[i].t >= 0 && stats[i].z > z) {
+      z = stats[i].z;
+      bi = i;
+    }
+  }
+  zb[threadIdx.x] = z;
+  ib[threadIdx.x] = bi;
+  __syncthreads();
+  for (int h = NT / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      const double zo = zb[threadIdx.x + h];
+      const int io = ib[threadIdx.x + h];
+      if (io >= 0 && (ib[threadIdx.x] < 0 || zo > zb[threadIdx.x] || (zo == zb[threadIdx.x] && io < ib[threadIdx.x]))) {
+        zb[threadIdx.x] = zo;
+        ib[threadIdx.x] = io;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    dd_snr_result r{};
+    const int b = ib[0];
+    if (b >= 0) {
+      r.snr = stats[b].z;
+      r.loss = -stats[b].z;
+      r.mean = stats[b].mean;
+      r.std = stats[b].sd;
+      r.best_t = stats[b].t;
+      r.best_row = b;
+      r.valid = 1;
+    } else {
+      r.best_row = -1;
+      r.best_t = -1;
+      r.valid = 0;
+    }
+    *result = r;
+  }
+}
+
+// d loss / d x for the best row (the other rows were zeroed by the caller).
+__global__ void snr_grad_kernel(const float* __restrict__ x, int64_t stride, int64_t n_cols,
+                                const dd_snr_result* __restrict__ result, float* __restrict__ grad,
+                                int64_t grad_stride) {
+  const dd_snr_result r = *result;
+  if (!r.valid) return;
+  const int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= n_cols) return;
+  const float* row = x + (int64_t)r.best_row * stride;
+  const int64_t nb = n_cols - kBox + 1;
+  double acc = 0.0;
+  const int64_t t_lo = u - (kBox - 1) > 0 ? u - (kBox - 1) : 0;
+  const int64_t t_hi = u < nb - 1 ? u : nb - 1;
+  for (int64_t t = t_lo; t <= t_hi; ++t) {
+    const double z = (boxcar(row, t) - r.mean) / r.std;
+    acc += ((t == r.best_t ? 1.0 : 0.0) - 1.0 / (double)nb) / r.std - r.snr * z / ((double)nb * r.std);
+  }
+  grad[(int64_t)r.best_row * grad_stride + u] = (float)(-acc);
+}
+
+dd_status boxcar_snr_launch(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols, dd_snr_result* result,
+                            float* grad, int64_t grad_stride, cudaStream_t s, void* scratch) {
+  constexpr int NT = 256;
+  RowStat* stats = static_cast<RowStat*>(scratch);
+  snr_rows_kernel<NT><<<n_rows, NT, 0, s>>>(x, row_stride, n_cols, stats);
+  snr_pick_kernel<NT><<<1, NT, 0, s>>>(stats, n_rows, result);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess && grad) {
+    e = cudaMemset2DAsync(grad, grad_stride * sizeof(float), 0, n_cols * sizeof(float), n_rows, s);
+    if (e == cudaSuccess) {
+      snr_grad_kernel<<<(unsigned)((n_cols + 255) / 256), 256, 0, s>>>(x, row_stride, n_cols, result, grad,
+                                                                         grad_stride);
+      e = cudaGetLastError();
+    }
+  }
+  if (e != cudaSuccess) return set_cuda_error("dd_boxcar_snr: launch", e);
+  return DD_OK;
+}
+
+dd_status boxcar_snr_check(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
+                           const dd_snr_result* result, const float* grad, int64_t grad_stride) {
+  if (!x || !result) return set_error(DD_ERR_ARG, "dd_boxcar_snr: x/result is NULL");
+  if (n_rows <= 0) return set_error(DD_ERR_ARG, "dd_boxcar_snr: n_rows must be > 0");
+  if (n_cols < kBox) return set_error(DD_ERR_SHAPE, "dd_boxcar_snr: n_cols must be >= %d", kBox);
+  if (row_stride < n_cols) return set_error(DD_ERR_SHAPE, "dd_boxcar_snr: row_stride < n_cols");
+  if (grad && grad_stride < n_cols) return set_error(DD_ERR_SHAPE, "dd_boxcar_snr: grad_stride < n_cols");
+  return DD_OK;
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" dd_status dd_boxcar_snr(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
+                                   dd_snr_result* result, float* grad, int64_t grad_stride, void* stream) {
+  clear_error();
+  dd_status st = boxcar_snr_check(x, row_stride, n_rows, n_cols, result, grad, grad_stride);
+  if (st != DD_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  void* scratch = nullptr;
+  const size_t bytes = (size_t)n_rows * sizeof(RowStat);
+  if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess)
+    return set_error(DD_ERR_NOMEM, "dd_boxcar_snr: cannot allocate %zu bytes of scratch", bytes);
+  st = boxcar_snr_launch(x, row_stride, n_rows, n_cols, result, grad, grad_stride, s, scratch);
+  cudaFreeAsync(scratch, s);
+  return st;
+}
