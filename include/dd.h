@@ -216,6 +216,32 @@ typedef struct {
 dd_status dd_boxcar_snr(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
                         dd_snr_result* result, float* grad, int64_t grad_stride, void* stream);
 
+/*
+ * dd_boxcar_snr for callers that must not allocate memory.  The paper has no
+ * counterpart: this entry point exists only for how the library is embedded.
+ * Some callers cannot call cudaMalloc or any allocator once they are running:
+ * a real-time pipeline that reserved all of its device memory at start-up
+ * and cannot afford an allocator call (which may synchronise the device or
+ * fail) on its hot path, or a host framework that owns every device
+ * allocation itself and does not let plug-ins allocate.  This call does the
+ * same computation with the same arguments and results as dd_boxcar_snr but
+ * allocates nothing: its per-row scratch lives in a fixed array inside the
+ * library, DD_NOALLOC_MAX_ROWS rows of 32 bytes (2 MiB), which every GPU that
+ * loads the library holds until the process exits.
+ *  - n_rows > DD_NOALLOC_MAX_ROWS is rejected with DD_ERR_SHAPE.
+ *  - The first call on a device looks up that array's device address (once
+ *    per device, with the device current); make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array and it keeps the previous
+ *    call's contents; nothing in it needs to start at zero (each call writes
+ *    every entry it reads).  Calls that can overlap on the GPU (different
+ *    streams, or different host threads on the same device) race on it and
+ *    must be serialised by the caller.
+ */
+#define DD_NOALLOC_MAX_ROWS 65536
+dd_status dd_boxcar_snr_noalloc(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
+                                dd_snr_result* result, float* grad, int64_t grad_stride, void* stream);
+
 /* --------------------------------------------------------------- batching */
 
 /*

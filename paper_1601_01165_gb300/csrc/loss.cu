@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cfloat>
+#include <mutex>
 
 #include "dd_errors.h"
 #include "dd_internal.h"
@@ -207,4 +208,51 @@ extern "C" dd_status dd_boxcar_snr(const float* x, int64_t row_stride, int32_t n
   st = boxcar_snr_launch(x, row_stride, n_rows, n_cols, result, grad, grad_stride, s, scratch);
   cudaFreeAsync(scratch, s);
   return st;
+}
+
+// ------------------------------------------------------ allocation-free form
+// Per-row scratch for dd_boxcar_snr_noalloc.  It is part of the library image,
+// so each GPU that loads the library carries it (2 MiB) until the process
+// exits, and no call ever has to allocate.  Host code cannot use the symbol
+// itself as a device address: the address is looked up per device below.
+namespace dd {
+static __device__ __align__(256) RowStat g_noalloc_rows[DD_NOALLOC_MAX_ROWS];
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of g_noalloc_rows on the current device, looked up on the
+// first call for that device.
+static dd_status noalloc_rows(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return set_cuda_error("dd_boxcar_snr_noalloc: cudaGetDevice", e);
+  if (dev < 0 || dev >= kNoAllocMaxDevices)
+    return set_error(DD_ERR_UNSUPPORTED, "dd_boxcar_snr_noalloc: device %d is beyond the %d supported", dev,
+                     kNoAllocMaxDevices);
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_rows);
+    if (e != cudaSuccess || !p) return set_cuda_error("dd_boxcar_snr_noalloc: cudaGetSymbolAddress", e);
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return DD_OK;
+}
+}  // namespace dd
+
+extern "C" dd_status dd_boxcar_snr_noalloc(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
+                                           dd_snr_result* result, float* grad, int64_t grad_stride, void* stream) {
+  clear_error();
+  dd_status st = boxcar_snr_check(x, row_stride, n_rows, n_cols, result, grad, grad_stride);
+  if (st != DD_OK) return st;
+  if (n_rows > DD_NOALLOC_MAX_ROWS)
+    return set_error(DD_ERR_SHAPE, "dd_boxcar_snr_noalloc: %d rows exceed the fixed scratch of %d rows", n_rows,
+                     DD_NOALLOC_MAX_ROWS);
+  void* rows = nullptr;
+  st = noalloc_rows(&rows);
+  if (st != DD_OK) return st;
+  return boxcar_snr_launch(x, row_stride, n_rows, n_cols, result, grad, grad_stride,
+                           static_cast<cudaStream_t>(stream), rows);
 }
