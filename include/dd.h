@@ -255,7 +255,12 @@ dd_status dd_boxcar_snr_noalloc(const float* x, int64_t row_stride, int32_t n_ro
  * strides in_strides[b] / out_strides[b] (host arrays of n entries); results
  * are bit-identical to n separate dd_forward calls with the same plans and
  * NULL weights.  The first run on a stream captures the launch into a CUDA
- * graph keyed by the pointer set; later runs with the same pointers replay it.
+ * graph keyed by the pointer set; later runs with the same pointers replay it
+ * (a run on the legacy NULL stream launches without a graph).  Inputs must be
+ * 16-byte aligned with 16-byte row pitches (DD_ERR_ALIGN otherwise).  Runs of
+ * one batch must not overlap in time (they share the batch's work counters).
+ * An expired bounded wait inside the batch kernels is reported in the first
+ * plan's device status word (dd_plan_device_status).
  */
 dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, int32_t n);
 dd_status dd_batch_run(dd_batch_t batch, const void* const* ins, const int64_t* in_strides,

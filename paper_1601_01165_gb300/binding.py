@@ -308,3 +308,95 @@ def snr_result(raw) -> dict:
     b = bytes(raw.cpu().numpy().tobytes())
     vals = struct.unpack("<4dqii", b)
     return dict(zip(SNR_FIELDS, vals))
+
+
+class Batch:
+    """dd_batch_*: several beams' forward passes in one persistent launch (CUDA graph)."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        check(load().dd_batch_create(ctypes.byref(h), arr, len(self.plans)), "dd_batch_create")
+        self._h = h
+
+    def run(self, ins, outs, stream=None):
+        n = len(self.plans)
+        if len(ins) != n or len(outs) != n:
+            raise ValueError("one input and one output per beam")
+        for p, x, o in zip(self.plans, ins, outs):
+            _rows(x, "input", p.in_dtype, p.device)
+            _rows(o, "output", p.out_dtype, p.device)
+        vp = ctypes.c_void_p
+        i_arr = (vp * n)(*[x.data_ptr() for x in ins])
+        o_arr = (vp * n)(*[o.data_ptr() for o in outs])
+        is_arr = (ctypes.c_int64 * n)(*[x.stride(0) for x in ins])
+        os_arr = (ctypes.c_int64 * n)(*[o.stride(0) for o in outs])
+        check(load().dd_batch_run(self._h, i_arr, is_arr, o_arr, os_arr, _stream_handle(stream)), "dd_batch_run")
+        return outs
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dd_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Stream:
+    """dd_stream_*: chunked real-time dedispersion with the overlap tail kept on the device."""
+
+    def __init__(self, plan, chunk_len):
+        self.plan = plan
+        self.chunk_len = int(chunk_len)
+        h = ctypes.c_void_p()
+        check(load().dd_stream_create(ctypes.byref(h), plan.handle, self.chunk_len), "dd_stream_create")
+        self._h = h
+
+    def push(self, chunk, out=None, stream=None):
+        """Dedisperse the next chunk ([C][chunk_len], contiguous); returns (out, t0)."""
+        import torch
+        p = self.plan
+        if chunk.dtype != p.in_dtype or chunk.device != p.device or not chunk.is_contiguous() or \
+                tuple(chunk.shape) != (p.channels, self.chunk_len):
+            raise ValueError("chunk must be a contiguous [channels][chunk_len] tensor of the plan's type")
+        if out is None:
+            out = torch.empty((p.n_dm, self.chunk_len), dtype=p.out_dtype, device=p.device)
+        if not out.is_contiguous() or tuple(out.shape) != (p.n_dm, self.chunk_len):
+            raise ValueError("out must be a contiguous [n_dm][chunk_len] tensor")
+        t0 = ctypes.c_int64()
+        check(load().dd_stream_push(self._h, chunk.data_ptr(), out.data_ptr(), ctypes.byref(t0),
+                                    _stream_handle(stream)), "dd_stream_push")
+        return out, t0.value
+
+    def reset(self):
+        check(load().dd_stream_reset(self._h), "dd_stream_reset")
+
+    def state_bytes(self) -> int:
+        n = ctypes.c_int64()
+        check(load().dd_stream_state_bytes(self._h, ctypes.byref(n)), "dd_stream_state_bytes")
+        return n.value
+
+    def save(self, stream=None) -> bytes:
+        buf = ctypes.create_string_buffer(self.state_bytes())
+        check(load().dd_stream_save(self._h, buf, _stream_handle(stream)), "dd_stream_save")
+        return buf.raw
+
+    def restore(self, state: bytes, stream=None):
+        buf = ctypes.create_string_buffer(state, len(state))
+        check(load().dd_stream_restore(self._h, buf, _stream_handle(stream)), "dd_stream_restore")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().dd_stream_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -90,6 +90,8 @@ static int32_t build_group_desc(const dd_plan_s& p, std::vector<int4>& desc, int
   return worst;
 }
 
+int32_t block_spread_of(const dd_plan_s& p, int bd) { return block_spread(p, bd); }
+
 void free_plan_device(dd_plan_s* p) {
   cudaFree(p->d_delays);
   cudaFree(p->d_delaysT);

@@ -60,62 +60,73 @@ __global__ void __launch_bounds__(256) fwd_naive_kernel(FwdArgs a) {
 
 // ----------------------------------------------------------------- STAGED
 
-// Shared-memory layout of the staged kernels:
-//   [STAGES][CC][pitch] input spans (Tin), [STAGES][CC][BD] int32 delay
-//   slices, [STAGES] mbarriers.
+// Shared-memory layout of the staged kernels: kStBarBytes of mbarriers, then
+// [STAGES][CC][pitch] input spans (Tin) and [STAGES][CC][BD] int32 delay
+// slices.  The barriers come first so that a persistent block can work on
+// tiles of beams whose pitches differ.
+constexpr int kStBarBytes = 128;
 template <typename Tin>
 __host__ __device__ constexpr int staged_smem_bytes(int stages, int cc, int bd, int pitch) {
-  return stages * cc * pitch * (int)sizeof(Tin) + stages * cc * bd * 4 + stages * 8;
+  return kStBarBytes + stages * cc * pitch * (int)sizeof(Tin) + stages * cc * bd * 4;
 }
 
+__device__ __forceinline__ void init_stage_bars(uint64_t* bars, int stages) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+}
+
+// One tile: DM trials [by*BD, by*BD + BD) x samples [bx*BT, bx*BT + BT).
+// `kbase` counts the chunks this block consumed before the tile, so the
+// stage barriers' phases carry on across the tiles of a persistent block.
+// Returns false (on every thread) if a bounded wait expired.
 template <typename Tin, bool WEIGHTED, int BD, int BT, int CC, int STAGES>
-__global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
+__device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t bx, int by, uint32_t& kbase,
+                                            unsigned char* smem_raw) {
   using Tacc = typename AccOf<Tin>::type;
   constexpr int V = 16 / (int)sizeof(Tin);  // elements per 16 bytes
   constexpr int NW = 8;
   constexpr int DPW = BD / NW;
   constexpr int SPL = BT / 32;
   static_assert(BD % NW == 0 && BT % 32 == 0 && BD % 4 == 0, "tile shape");
+  static_assert(STAGES * 8 <= kStBarBytes, "barrier area");
 
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  Tin* sin = reinterpret_cast<Tin*>(smem_raw);
-  int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + (size_t)STAGES * CC * pitch * sizeof(Tin));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sdel + STAGES * CC * BD);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  Tin* sin = reinterpret_cast<Tin*>(smem_raw + kStBarBytes);
+  int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes + (size_t)STAGES * CC * pitch * sizeof(Tin));
 
   const Tin* __restrict__ in = static_cast<const Tin*>(a.in);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t t0 = (int64_t)blockIdx.x * BT;
-  const int i0 = blockIdx.y * BD;
+  const int64_t t0 = bx * BT;
+  const int i0 = by * BD;
   const int nt = (int)min((int64_t)BT, a.n_out - t0);
   const int nchunks = (a.C + CC - 1) / CC;
+  const uint32_t kb = kbase;
 
-  if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-
-  // Producer (thread 0): stage chunk k (channels [k*CC, k*CC + CC)) into stage k % STAGES.
+  // Producer (thread 0): stage chunk k (channels [k*CC, k*CC + CC)) into stage (kb + k) % STAGES.
   auto issue = [&](int k) {
-    const int s = k % STAGES;
+    const int s = (int)((kb + (uint32_t)k) % STAGES);
     const int c0 = k * CC;
     const int cn = min(CC, a.C - c0);
-    uint32_t bytes = 0;
-    for (int j = 0; j < cn; ++j) {
-      const int64_t c = c0 + j;
+    auto span = [&](int64_t c, int64_t& al, int64_t& ah) {
       const int64_t lo = t0 + __ldg(a.delaysT + c * a.n_dm_pad + i0);
       const int64_t hi = t0 + nt + __ldg(a.delaysT + c * a.n_dm_pad + i0 + BD - 1);
-      const int64_t al = lo & ~(int64_t)(V - 1);
-      const int64_t ah = (hi + V - 1) & ~(int64_t)(V - 1);
+      al = lo & ~(int64_t)(V - 1);
+      ah = (hi + V - 1) & ~(int64_t)(V - 1);
+    };
+    uint32_t bytes = 0;
+    for (int j = 0; j < cn; ++j) {
+      int64_t al, ah;
+      span(c0 + j, al, ah);
       bytes += (uint32_t)((ah - al) * (int64_t)sizeof(Tin)) + BD * 4;
     }
     mbar_arrive_expect_tx(&bars[s], bytes);
     for (int j = 0; j < cn; ++j) {
       const int64_t c = c0 + j;
-      const int64_t lo = t0 + __ldg(a.delaysT + c * a.n_dm_pad + i0);
-      const int64_t hi = t0 + nt + __ldg(a.delaysT + c * a.n_dm_pad + i0 + BD - 1);
-      const int64_t al = lo & ~(int64_t)(V - 1);
-      const int64_t ah = (hi + V - 1) & ~(int64_t)(V - 1);
+      int64_t al, ah;
+      span(c, al, ah);
       bulk_g2s(sin + (size_t)(s * CC + j) * pitch, in + c * a.in_stride + al,
                (uint32_t)((ah - al) * (int64_t)sizeof(Tin)), &bars[s]);
       bulk_g2s(sdel + (s * CC + j) * BD, a.delaysT + c * a.n_dm_pad + i0, BD * 4, &bars[s]);
@@ -133,17 +144,18 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
     for (int q = 0; q < SPL; ++q) acc[m][q] = 0;
 
   for (int k = 0; k < nchunks; ++k) {
-    const int s = k % STAGES;
-    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((k / STAGES) & 1), kWaitLimitCycles);
+    const uint32_t kg = kb + (uint32_t)k;
+    const int s = (int)(kg % STAGES);
+    const bool ok = mbar_wait_bounded(&bars[s], (kg / STAGES) & 1u, kWaitLimitCycles);
     // The barrier also tells every thread that chunk k-1 is fully consumed.
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         report_error(a.status, kDevWaitTimeout);
-        // let copies already in flight land before the block exits
+        // let copies already in flight land before the block moves on
         for (int kk = k; kk < min(k + STAGES, nchunks); ++kk)
-          (void)mbar_wait_bounded(&bars[kk % STAGES], (uint32_t)((kk / STAGES) & 1), kWaitLimitCycles);
+          (void)mbar_wait_bounded(&bars[(kb + kk) % STAGES], ((kb + kk) / STAGES) & 1u, kWaitLimitCycles);
       }
-      return;
+      return false;
     }
     if (tid == 0 && k >= 1 && k - 1 + STAGES < nchunks) issue(k - 1 + STAGES);
 
@@ -172,6 +184,7 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
       }
     }
   }
+  kbase = kb + (uint32_t)nchunks;
 
   Tacc* __restrict__ out = static_cast<Tacc*>(a.out);
 #pragma unroll
@@ -184,6 +197,39 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
         if (tt < nt) out[(int64_t)i * a.out_stride + t0 + tt] = acc[m][q];
       }
     }
+  }
+  return true;
+}
+
+template <typename Tin, bool WEIGHTED, int BD, int BT, int CC, int STAGES>
+__global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  init_stage_bars(reinterpret_cast<uint64_t*>(smem_raw), STAGES);
+  uint32_t kbase = 0;
+  (void)staged_tile<Tin, WEIGHTED, BD, BT, CC, STAGES>(a, pitch, blockIdx.x, blockIdx.y, kbase, smem_raw);
+}
+
+// Persistent form for batches of beams: each block pulls (beam, DM block,
+// time block) items from an atomic counter until the list is exhausted.
+template <typename Tin, int BD, int BT, int CC, int STAGES>
+__global__ void __launch_bounds__(256) fwd_staged_persistent(const BatchBeam* __restrict__ beams,
+                                                              const BatchItem* __restrict__ items, int n_items,
+                                                              int* counter, int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_item;
+  init_stage_bars(reinterpret_cast<uint64_t*>(smem_raw), STAGES);
+  uint32_t kbase = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();  // also: the previous tile is finished with shared memory
+    const int it = s_item;
+    __syncthreads();
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    const FwdArgs a = batch_args(beams[item.beam], status);
+    if (!staged_tile<Tin, false, BD, BT, CC, STAGES>(a, beams[item.beam].pitch, item.tile_t, item.tile_d, kbase,
+                                                     smem_raw))
+      break;
   }
 }
 
@@ -200,7 +246,8 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
 // 256 channels the packed sums are added into int32 totals and cleared: the
 // result is the exact integer sum.
 template <int WD, int WT, int DPW, int CC, int STAGES>
-__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int pitch) {
+__device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t bx, int by, uint32_t& kbase,
+                                          unsigned char* smem_raw) {
   constexpr int V = 16;
   constexpr int NW = WD * WT;
   constexpr int KW = 7;               // words per lane
@@ -209,27 +256,22 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
   constexpr int BT = 32 * SPL * WT;
   static_assert(BD % 4 == 0 && BT % 16 == 0, "tile shape");
 
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint8_t* sin = smem_raw;
-  int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + (size_t)STAGES * CC * pitch);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sdel + STAGES * CC * BD);
+  static_assert(STAGES * 8 <= kStBarBytes, "barrier area");
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  uint8_t* sin = smem_raw + kStBarBytes;
+  int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes + (size_t)STAGES * CC * pitch);
 
   const uint8_t* __restrict__ in = static_cast<const uint8_t*>(a.in);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wd = warp % WD, wt = warp / WD;
-  const int64_t t0 = (int64_t)blockIdx.x * BT;
-  const int i0 = blockIdx.y * BD;
+  const int64_t t0 = bx * BT;
+  const int i0 = by * BD;
   const int nt = (int)min((int64_t)BT, a.n_out - t0);
   const int nchunks = (a.C + CC - 1) / CC;
-
-  if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
+  const uint32_t kb = kbase;
 
   auto issue = [&](int k) {
-    const int s = k % STAGES;
+    const int s = (int)((kb + (uint32_t)k) % STAGES);
     const int c0 = k * CC;
     const int cn = min(CC, a.C - c0);
     auto span = [&](int64_t c, int64_t& al, int64_t& ah) {
@@ -296,15 +338,16 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
 
   int since_flush = 0;
   for (int k = 0; k < nchunks; ++k) {
-    const int s = k % STAGES;
-    const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((k / STAGES) & 1), kWaitLimitCycles);
+    const uint32_t kg = kb + (uint32_t)k;
+    const int s = (int)(kg % STAGES);
+    const bool ok = mbar_wait_bounded(&bars[s], (kg / STAGES) & 1u, kWaitLimitCycles);
     if (__syncthreads_or(!ok)) {
       if (tid == 0) {
         report_error(a.status, kDevWaitTimeout);
         for (int kk = k; kk < min(k + STAGES, nchunks); ++kk)
-          (void)mbar_wait_bounded(&bars[kk % STAGES], (uint32_t)((kk / STAGES) & 1), kWaitLimitCycles);
+          (void)mbar_wait_bounded(&bars[(kb + kk) % STAGES], ((kb + kk) / STAGES) & 1u, kWaitLimitCycles);
       }
-      return;
+      return false;
     }
     if (tid == 0 && k >= 1 && k - 1 + STAGES < nchunks) issue(k - 1 + STAGES);
     const int cn = min(CC, a.C - k * CC);
@@ -346,10 +389,11 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
     }
   }
   flush();
+  kbase = kb + (uint32_t)nchunks;
 
   // transpose through shared memory (stage area is free: every chunk was consumed)
   __syncthreads();
-  int32_t* epi = reinterpret_cast<int32_t*>(smem_raw) + (size_t)warp * DPW * 32 * SPL;
+  int32_t* epi = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes) + (size_t)warp * DPW * 32 * SPL;
 #pragma unroll
   for (int m = 0; m < DPW; ++m)
 #pragma unroll
@@ -364,12 +408,42 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
     int32_t* orow = out + (int64_t)i * a.out_stride + t0 + tw0;
     for (int u = lane; u < lim; u += 32) orow[u] = epi[m * 32 * SPL + u];
   }
+  return true;
+}
+
+template <int WD, int WT, int DPW, int CC, int STAGES>
+__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int pitch) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  init_stage_bars(reinterpret_cast<uint64_t*>(smem_raw), STAGES);
+  uint32_t kbase = 0;
+  (void)u8pk_tile<WD, WT, DPW, CC, STAGES>(a, pitch, blockIdx.x, blockIdx.y, kbase, smem_raw);
+}
+
+template <int WD, int WT, int DPW, int CC, int STAGES>
+__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_persistent(const BatchBeam* __restrict__ beams,
+                                                                     const BatchItem* __restrict__ items, int n_items,
+                                                                     int* counter, int* status) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int s_item;
+  init_stage_bars(reinterpret_cast<uint64_t*>(smem_raw), STAGES);
+  uint32_t kbase = 0;
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();  // also: the previous tile is finished with shared memory
+    const int it = s_item;
+    __syncthreads();
+    if (it >= n_items) break;
+    const BatchItem item = items[it];
+    const FwdArgs a = batch_args(beams[item.beam], status);
+    if (!u8pk_tile<WD, WT, DPW, CC, STAGES>(a, beams[item.beam].pitch, item.tile_t, item.tile_d, kbase, smem_raw))
+      break;
+  }
 }
 
 __host__ __device__ constexpr int u8pk_smem_bytes(int stages, int cc, int bd, int pitch, int nw, int dpw) {
-  return (stages * cc * pitch + stages * cc * bd * 4 + stages * 8) > nw * dpw * 32 * 28 * 4
-             ? (stages * cc * pitch + stages * cc * bd * 4 + stages * 8)
-             : nw * dpw * 32 * 28 * 4;
+  return (stages * cc * pitch + stages * cc * bd * 4) > nw * dpw * 32 * 28 * 4
+             ? kStBarBytes + (stages * cc * pitch + stages * cc * bd * 4)
+             : kStBarBytes + nw * dpw * 32 * 28 * 4;
 }
 
 // --------------------------------------------------------------- dispatch
@@ -498,6 +572,53 @@ int u8pk_smem_for(const TileConfig& cfg, int pitch) {
 int staged_smem_for(dd_dtype dtype, int stages, int cc, int bd, int pitch) {
   return dtype == DD_U8_I32 ? staged_smem_bytes<uint8_t>(stages, cc, bd, pitch)
                             : staged_smem_bytes<float>(stages, cc, bd, pitch);
+}
+
+// ------------------------------------------------------------------ batches
+// Tile shapes of the persistent batch kernels (the measured-fastest STAGED
+// and U8PK shapes on the Apertif setup).
+#define DD_BATCH_F32 8, 1024, 4, 3       /* BD, BT, CC, STAGES */
+#define DD_BATCH_U8 8, 1, 2, 16, 4       /* WD, WT, DPW, CC, STAGES */
+
+TileConfig batch_config(dd_dtype dtype) {
+  if (dtype == DD_U8_I32) return {Kind::U8Pk, 16, 32 * 28, 16, 4, 256, 28, 0, 0, "u8pk_w8x1_d2_c16_st4"};
+  return {Kind::Staged, 8, 1024, 4, 3, 256, 0, 0, 0, "staged_d8_t1024_c4_s3"};
+}
+
+int batch_smem_for(dd_dtype dtype, int pitch) {
+  if (dtype == DD_U8_I32) return u8pk_smem_bytes(4, 16, 16, pitch, 8, 2);
+  return staged_smem_bytes<float>(3, 4, 8, pitch);
+}
+
+int batch_blocks_per_sm(dd_dtype dtype, int smem) {
+  int n = 0;
+  cudaError_t e;
+  if (dtype == DD_U8_I32) {
+    auto k = fwd_u8pk_persistent<DD_BATCH_U8>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, smem);
+  } else {
+    auto k = fwd_staged_persistent<float, DD_BATCH_F32>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, smem);
+  }
+  return e == cudaSuccess ? n : 0;
+}
+
+cudaError_t launch_batch(dd_dtype dtype, const BatchBeam* beams, const BatchItem* items, int n_items, int* counter,
+                         int* status, int smem, int grid, cudaStream_t s) {
+  if (dtype == DD_U8_I32) {
+    auto k = fwd_u8pk_persistent<DD_BATCH_U8>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 256, smem, s>>>(beams, items, n_items, counter, status);
+  } else {
+    auto k = fwd_staged_persistent<float, DD_BATCH_F32>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, 256, smem, s>>>(beams, items, n_items, counter, status);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace dd
