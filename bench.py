@@ -44,7 +44,12 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
 # keyed by (kernel config, dtype); valid only while the kernel source hash matches.
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {
+    # profiles/fwd_staged_f32_apertif.md: 747.2 MB read + 158.8 MB written
+    ("staged_d8_t1024_c4_s3", "f32"): {"bytes": 906_023_424, "hash": "654b5a1630a85393"},
+    # profiles/fwd_u8pk_u8_apertif.md: 32.6 MB read + 112.9 MB written
+    ("u8pk_w8x1_d2_c16_st4", "u8"): {"bytes": 145_405_440, "hash": "654b5a1630a85393"},
+}
 
 
 def _peaks():
@@ -58,12 +63,12 @@ def _peaks():
 
 
 def _kernel_hash():
+    """Hash of the sources the forward kernels are built from (traffic figures are tied to it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_01165_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h", ".cpp")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(f.read())
+    for name in ("fwd_kernels.cu", "fwd_tmrw.cu", "fwd_regwin.cu", "ptx.cuh", "dd_internal.h"):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -334,6 +339,99 @@ def run_ours(args, setup):
     return 0
 
 
+def run_batched(args):
+    """64 uneven beams: one persistent launch (CUDA graph) vs 64 plain launches of the same plans."""
+    import torch
+    from paper_1601_01165_gb300 import binding as dd
+    torch.cuda.set_device(0)
+    beams = synth.batched_setups(args.seed, args.beams)
+    plans, xs, outs = [], [], []
+    g = torch.Generator(device="cuda").manual_seed(args.seed)
+    for s, dt in beams:
+        p = dd.Plan.from_setup(s, dt)
+        x = torch.empty((s.channels, p.padded_in_stride()), dtype=p.in_dtype, device="cuda")
+        if dt == "u8":
+            x.copy_(torch.randint(0, 256, x.shape, generator=g, device="cuda", dtype=torch.int32).to(torch.uint8))
+        else:
+            x.normal_(generator=g)
+        plans.append(p)
+        xs.append(x)
+        outs.append(torch.empty((s.n_dm, s.n_out), dtype=p.out_dtype, device="cuda"))
+    batch = dd.Batch(plans)
+    stream = torch.cuda.Stream()
+    units = sum(s.n_dm * s.n_out for s, _ in beams)
+    adds = sum(s.adds for s, _ in beams)
+
+    def timed(fn, k):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for _ in range(args.warmup):
+                fn()
+            stream.synchronize()
+            ev0.record(stream)
+            for _ in range(k):
+                fn()
+            ev1.record(stream)
+        stream.synchronize()
+        return ev0.elapsed_time(ev1) / k
+
+    def run_batch():
+        batch.run(xs, outs, stream=stream)
+
+    def run_plain():
+        for p, x, o in zip(plans, xs, outs):
+            p.forward(x, out=o, stream=stream)
+
+    ms_batch = timed(run_batch, args.steps)
+    ms_plain = timed(run_plain, args.steps)
+    # the batch's results equal the per-beam launches (checked on every beam)
+    with torch.cuda.stream(stream):
+        run_batch()
+        ref = [p.forward(x, stream=stream) for p, x in zip(plans, xs)]
+    stream.synchronize()
+    same = all(torch.equal(o, r) for o, r in zip(outs, ref))
+    line = {"metric": METRIC, "workload": "batched", "value": units / (ms_batch / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
+            "plain_launches_ms": ms_plain, "speedup_vs_plain": ms_plain / ms_batch, "beams": len(beams),
+            "adds_per_step": adds, "batch_equals_plain": same, "gpu_launches": 2 * args.steps,
+            "config": {"workload": f"{len(beams)} uneven beams (channels 32/256/1024, DMs 256/1024/4096, "
+                                   f"10k-200k samples, Apertif/LOFAR grids, mixed uint8/float32), seed {args.seed}"}}
+    print(json.dumps(line), flush=True)
+    return 0 if same else 1
+
+
+def run_serving(args):
+    """Real-time serving: Apertif-like uint8 beams delivering 1 s chunks on independent timers."""
+    import torch
+    from paper_1601_01165_gb300.serve import BeamSpec, Server, beam_bytes
+    torch.cuda.set_device(0)
+    base = synth.APERTIF
+    rng = np.random.default_rng(args.seed)
+    specs = [BeamSpec(f"beam{b}", base, "u8", chunk_len=base.n_out, n_chunks=args.chunks,
+                      period_s=base.n_out * base.t_samp_s, phase_s=float(rng.uniform(0, 1)))
+             for b in range(args.beams)]
+    cache = {}
+
+    def source(sp, k):
+        key = k % 4
+        if key not in cache:
+            cache[key] = synth.noise_u8(args.seed + key, base.channels, base.n_out)
+        return cache[key]
+
+    budget = int(args.budget_gb * 2**30) if args.budget_gb else args.beams * beam_bytes(specs[0]) + 1
+    rep = Server(budget).run(specs, source)
+    line = {"metric": METRIC, "workload": "serving", "unit": UNIT, "n_gpus": 1,
+            "value": rep["throughput_dm_samples_per_s"], "beams": args.beams, "chunks": rep["chunks"],
+            "latency_p50_s": rep["latency_p50_s"], "latency_p99_s": rep["latency_p99_s"],
+            "latency_max_s": rep["latency_max_s"], "deadline_s": specs[0].period_s,
+            "deadline_misses": rep["deadline_misses"], "peak_beams": rep["peak_beams"],
+            "peak_bytes": rep["peak_bytes"], "budget_bytes": rep["budget_bytes"],
+            "config": {"workload": f"{args.beams} Apertif-like uint8 beams, 1 s chunks ({base.n_out} samples), "
+                                   f"{args.chunks} chunks each, random phases, HBM budget {budget / 2**30:.1f} GiB"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def _make_input(setup, dtype, seed, n_in, stride, d):
     x = (synth.noise_u8 if dtype == "u8" else synth.noise_f32)(seed, setup.channels, n_in, stride)
     for i_p, t_p in synth.pulse_sites(seed, setup.n_dm, setup.n_out, 3):
@@ -349,12 +447,22 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--dtype", choices=["f32", "u8"], default="f32")
     ap.add_argument("--config", default=None, help="kernel configuration name (default: plan's choice)")
-    ap.add_argument("--workload", choices=["apertif", "lofar"], default="apertif")
+    ap.add_argument("--workload", choices=["apertif", "lofar", "batched", "serving"], default="apertif")
+    ap.add_argument("--beams", type=int, default=None, help="batched: 64, serving: 40")
+    ap.add_argument("--chunks", type=int, default=4, help="serving: chunks per beam")
+    ap.add_argument("--budget-gb", type=float, default=None, help="serving: HBM budget")
+    ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.workload == "batched":
+        args.beams = args.beams or 64
+        return run_batched(args)
+    if args.workload == "serving":
+        args.beams = args.beams or 40
+        return run_serving(args)
     setup = synth.APERTIF if args.workload == "apertif" else synth.LOFAR
     if args.impl == "reference":
         return run_reference(args, setup)

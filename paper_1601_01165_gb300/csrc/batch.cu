@@ -2,11 +2,11 @@
 // independently; Section 5.1: one device dedisperses many beams) in one
 // persistent launch per input type, captured in a CUDA graph.
 //
-// dd_batch_create turns the beams' plans into one work list of (beam, DM
-// block, time block) tiles, longest beam first (per-tile cost grows with the
-// beam's channel count, so big beams start early and small ones fill the
-// tail), and sizes a persistent grid from the occupancy of the widest beam's
-// shared-memory need.  dd_batch_run writes the beams' pointers into a device
+// dd_batch_create sorts the beams into groups by input type and by how many
+// blocks per SM their shared-memory need allows, and turns each group into a
+// work list of (beam, DM block, time block) tiles, longest beam first (big
+// beams start early, small ones fill the tail) with a persistent grid sized
+// by that occupancy.  dd_batch_run writes the beams' pointers into a device
 // descriptor table and launches; the launch sequence (counter reset +
 // persistent kernels) is captured once per (pointer set, stream) and replayed
 // afterwards.  Every tile is computed exactly as the solo kernels do, so a
@@ -102,57 +102,74 @@ extern "C" dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, in
     delete b;
     return set_cuda_error("dd_batch_create: device query", e);
   }
+  // One group per (input type, occupancy class): beams whose shared-memory
+  // need allows the same number of resident blocks per SM share a persistent
+  // launch, so a wide-spread beam does not lower the occupancy of the others.
   for (dd_dtype dt : {DD_F32_F32, DD_U8_I32}) {
-    dd_batch_s::Group g;
-    g.dtype = dt;
-    g.cfg = batch_config(dt);
-    for (int32_t k = 0; k < n; ++k)
-      if (plans[k]->dtype == dt) g.beams.push_back(k);
-    if (g.beams.empty()) continue;
-    // longest beams first (largest C * n_dm * n_out)
-    std::stable_sort(g.beams.begin(), g.beams.end(), [&](int x, int y) {
-      const double cx = (double)plans[x]->C * plans[x]->n_dm * plans[x]->n_out;
-      const double cy = (double)plans[y]->C * plans[y]->n_dm * plans[y]->n_out;
-      return cx > cy;
-    });
+    const TileConfig cfg = batch_config(dt);
     const int V = dt == DD_U8_I32 ? 16 : 4;
     const int slack = dt == DD_U8_I32 ? 32 : 0;
-    std::vector<BatchItem> items;
-    for (size_t j = 0; j < g.beams.size(); ++j) {
-      const dd_plan_s& p = *plans[g.beams[j]];
-      const int64_t spread = block_spread_of(p, g.cfg.bd);
-      const int64_t pitch = (g.cfg.bt + spread + 2 * V + slack + V - 1) / V * V;
+    struct BeamInfo {
+      int k, pitch, smem, per_sm;
+      double cost;
+    };
+    std::vector<BeamInfo> infos;
+    for (int32_t k = 0; k < n; ++k) {
+      const dd_plan_s& p = *plans[k];
+      if (p.dtype != dt) continue;
+      const int64_t spread = block_spread_of(p, cfg.bd);
+      const int64_t pitch = (cfg.bt + spread + 2 * V + slack + V - 1) / V * V;
       const int smem = batch_smem_for(dt, (int)pitch);
       if (smem > kMaxSmemPerBlock) {
         free_batch(b);
         delete b;
-        return set_error(DD_ERR_UNSUPPORTED, "dd_batch_create: beam %d needs %d bytes of shared memory", g.beams[j],
-                         smem);
+        return set_error(DD_ERR_UNSUPPORTED, "dd_batch_create: beam %d needs %d bytes of shared memory", k, smem);
       }
-      g.pitch.push_back((int)pitch);
-      g.smem = std::max(g.smem, smem);
-      const int32_t td = (p.n_dm + g.cfg.bd - 1) / g.cfg.bd;
-      const int64_t tt = (p.n_out + g.cfg.bt - 1) / g.cfg.bt;
-      for (int32_t d = 0; d < td; ++d)
-        for (int64_t t = 0; t < tt; ++t) items.push_back(BatchItem{(int32_t)j, d, (int32_t)t, 0});
+      infos.push_back({k, (int)pitch, smem, std::max(1, batch_blocks_per_sm(dt, smem)),
+                       (double)p.C * p.n_dm * p.n_out});
     }
-    if (items.size() > (size_t)INT32_MAX) {
-      free_batch(b);
-      delete b;
-      return set_error(DD_ERR_UNSUPPORTED, "dd_batch_create: too many tiles");
-    }
-    g.n_items = (int)items.size();
-    const int per_sm = std::max(1, batch_blocks_per_sm(dt, g.smem));
-    g.grid = std::max(1, std::min(sms * per_sm, g.n_items));
-    e = cudaMalloc(&g.d_items, items.size() * sizeof(BatchItem));
-    if (e == cudaSuccess) e = cudaMemcpy(g.d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&g.d_beams, g.beams.size() * sizeof(BatchBeam));
-    if (e == cudaSuccess) e = cudaMallocHost(&g.h_beams, g.beams.size() * sizeof(BatchBeam));
-    b->groups.push_back(g);
-    if (e != cudaSuccess) {
-      free_batch(b);
-      delete b;
-      return set_error(DD_ERR_NOMEM, "dd_batch_create: allocation failed");
+    std::vector<int> classes;
+    for (const auto& bi : infos)
+      if (std::find(classes.begin(), classes.end(), bi.per_sm) == classes.end()) classes.push_back(bi.per_sm);
+    std::sort(classes.begin(), classes.end());
+    for (int per_sm : classes) {
+      dd_batch_s::Group g;
+      g.dtype = dt;
+      g.cfg = cfg;
+      std::vector<BeamInfo> mine;
+      for (const auto& bi : infos)
+        if (bi.per_sm == per_sm) mine.push_back(bi);
+      // longest beams first (largest C * n_dm * n_out)
+      std::stable_sort(mine.begin(), mine.end(), [](const BeamInfo& x, const BeamInfo& y) { return x.cost > y.cost; });
+      std::vector<BatchItem> items;
+      for (size_t j = 0; j < mine.size(); ++j) {
+        const dd_plan_s& p = *plans[mine[j].k];
+        g.beams.push_back(mine[j].k);
+        g.pitch.push_back(mine[j].pitch);
+        g.smem = std::max(g.smem, mine[j].smem);
+        const int32_t td = (p.n_dm + cfg.bd - 1) / cfg.bd;
+        const int64_t tt = (p.n_out + cfg.bt - 1) / cfg.bt;
+        for (int32_t d = 0; d < td; ++d)
+          for (int64_t t = 0; t < tt; ++t) items.push_back(BatchItem{(int32_t)j, d, (int32_t)t, 0});
+      }
+      if (items.size() > (size_t)INT32_MAX) {
+        free_batch(b);
+        delete b;
+        return set_error(DD_ERR_UNSUPPORTED, "dd_batch_create: too many tiles");
+      }
+      g.n_items = (int)items.size();
+      g.grid = std::max(1, std::min(sms * per_sm, g.n_items));
+      e = cudaMalloc(&g.d_items, items.size() * sizeof(BatchItem));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(g.d_items, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMalloc(&g.d_beams, g.beams.size() * sizeof(BatchBeam));
+      if (e == cudaSuccess) e = cudaMallocHost(&g.h_beams, g.beams.size() * sizeof(BatchBeam));
+      b->groups.push_back(g);
+      if (e != cudaSuccess) {
+        free_batch(b);
+        delete b;
+        return set_error(DD_ERR_NOMEM, "dd_batch_create: allocation failed");
+      }
     }
   }
   b->d_status = plans[0]->d_status;

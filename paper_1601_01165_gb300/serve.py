@@ -68,6 +68,7 @@ class _Active:
         in_dt = self.plan.in_dtype
         self.d_chunk = torch.empty((s.channels, spec.chunk_len), dtype=in_dt, device=device)
         self.d_out = torch.empty((s.n_dm, spec.chunk_len), dtype=self.plan.out_dtype, device=device)
+        self.h_in = torch.empty((s.channels, spec.chunk_len), dtype=in_dt, pin_memory=True)
         self.h_out = torch.empty((s.n_dm, spec.chunk_len), dtype=self.plan.out_dtype, pin_memory=True)
         self.pending = None          # (chunk index, arrival, t0, event)
         self.next_chunk = 0
@@ -140,6 +141,7 @@ class Server:
                 in_use += need[sp.name]
                 peak_in_use = max(peak_in_use, in_use)
                 peak_beams = max(peak_beams, len(active))
+                now = time.perf_counter()     # the beam's clock starts once its resources exist
                 admitted_at[sp.name] = now
                 for k in range(sp.n_chunks):
                     heapq.heappush(arrivals, (now + (sp.phase_s + k * sp.period_s) * time_scale, sp.name, k))
@@ -159,7 +161,8 @@ class Server:
                         still.append((arr, name, k))
                         continue
                     host = chunk_source(act.spec, k)
-                    h = torch.from_numpy(np.ascontiguousarray(host)).pin_memory()
+                    h = act.h_in
+                    h.copy_(torch.from_numpy(np.ascontiguousarray(host)))
                     with torch.cuda.stream(act.cuda_stream):
                         act.d_chunk.copy_(h, non_blocking=True)
                         _, t0 = act.state.push(act.d_chunk, out=act.d_out, stream=act.cuda_stream)
