@@ -66,7 +66,7 @@ def _kernel_hash():
     """Hash of the sources the forward kernels are built from (traffic figures are tied to it)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_01165_gb300", "csrc")
-    for name in ("fwd_kernels.cu", "fwd_tmrw.cu", "fwd_regwin.cu", "ptx.cuh", "dd_internal.h"):
+    for name in ("fwd_kernels.cu", "fwd_tmw6.cu", "ptx.cuh", "dd_internal.h"):
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]

@@ -217,7 +217,8 @@ class Plan:
         return torch.zeros((self.channels, stride), dtype=self.in_dtype, device=self.device)
 
     def padded_in_stride(self) -> int:
-        v = 16 if self.dtype == "u8" else 4
+        """Row stride (elements) giving 128-byte input rows, which every kernel accepts."""
+        v = 128 if self.dtype == "u8" else 32
         return (self.n_in + v - 1) // v * v
 
     def forward(self, x, w=None, out=None, stream=None):

@@ -51,8 +51,7 @@ dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const 
   a.out_stride = out_stride;
   a.delays = p->d_delays;
   a.delaysT = p->d_delaysT;
-  a.regwin_desc = p->d_regwin_desc;
-  a.quad_desc = p->d_quad_desc;
+  a.hex_desc = p->d_hex_desc;
   a.C = p->C;
   a.n_dm = p->n_dm;
   a.n_dm_pad = p->n_dm_pad;
@@ -64,13 +63,14 @@ dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const 
   // Bulk copies need a 16-byte aligned source and row pitch; otherwise use the
   // plain-load kernel, which computes the same sums.
   const bool aligned = ((uintptr_t)in % 16 == 0) && ((in_stride * elem) % 16 == 0);
-  if (cfg->kind != Kind::Naive && !aligned) {
+  auto first_of = [&](Kind kind) -> const TileConfig* {
     for (size_t j = 0; j < p->configs.size(); ++j)
-      if (p->configs[j].kind == Kind::Naive) {
-        cfg = &p->configs[j];
-        break;
-      }
-  }
+      if (p->configs[j].kind == kind) return &p->configs[j];
+    return nullptr;
+  };
+  if (cfg->kind != Kind::Naive && !aligned) cfg = first_of(Kind::Naive);
+  // TMCP stages 128-byte rows; other layouts take the shared-memory kernel
+  if (cfg->kind == Kind::TmW6 && !tmw6_accepts(in, in_stride)) cfg = &p->configs[p->fallback];
   cudaError_t e = launch_forward(*cfg, p->dtype, a, stream);
   if (e != cudaSuccess) return set_cuda_error("dd_forward: launch", e);
   return DD_OK;
@@ -116,8 +116,8 @@ extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_
     return set_error(DD_ERR_UNSUPPORTED, "dd_forward_host: uint8 plans take unit weights only");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t elem = plan->dtype == DD_U8_I32 ? 1 : 4;
-  // device rows padded to 16 bytes so the staged kernels apply
-  const int64_t dev_in_stride = (plan->n_in * (int64_t)elem + 15) / 16 * 16 / (int64_t)elem;
+  // device rows padded to 128 bytes so every staged kernel applies
+  const int64_t dev_in_stride = (plan->n_in * (int64_t)elem + 127) / 128 * 128 / (int64_t)elem;
   const size_t in_bytes = (size_t)plan->C * dev_in_stride * elem;
   const size_t out_bytes = (size_t)plan->n_dm * plan->n_out * 4;
   if (plan->h_in_bytes < in_bytes) {

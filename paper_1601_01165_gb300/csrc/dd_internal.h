@@ -13,10 +13,10 @@ namespace dd {
 // Forward kernel families.  NAIVE is the paper's "generically tuned" layout
 // (Section 5: one DM per thread, 1-D blocks, no explicit data reuse); STAGED is
 // the 2-D (DM x time) block of Section 2.2 with each channel's input span
-// staged in shared memory by bulk copies; REGWIN adds reuse in registers across
-// a warp's group of DM trials; TMRW does that reuse through Tensor Memory;
-// U8PK is the uint8 path with packed 16-bit integer sums.
-enum class Kind : int { Naive = 0, Staged = 1, RegWin = 2, TmRw = 3, U8Pk = 4 };
+// staged in shared memory by bulk copies; U8PK is the uint8 path with packed
+// 16-bit integer sums; TMW6 (float) shares each channel's input window among
+// 6 DM trials through Tensor Memory.
+enum class Kind : int { Naive = 0, Staged = 1, U8Pk = 4, TmW6 = 7 };
 
 struct TileConfig {
   Kind kind;
@@ -25,7 +25,7 @@ struct TileConfig {
   int cc;       // channels per pipeline stage
   int stages;   // pipeline depth
   int threads;  // threads per block
-  int spl;      // REGWIN / TMRW: samples per lane
+  int spl;      // TMW6: samples per lane
   int smem;     // dynamic shared memory bytes (filled per plan)
   int pitch;    // staged row pitch in elements (filled per plan)
   std::string name;
@@ -40,8 +40,7 @@ struct FwdArgs {
   int64_t out_stride;
   const int32_t* delays;   // [n_dm][C]
   const int32_t* delaysT;  // [C][n_dm_pad], DMs >= n_dm repeat the last trial
-  const int4* regwin_desc; // 8-trial group descriptors [C][n_dm_pad / 8]
-  const int4* quad_desc;   // 4-trial group descriptors [C][n_dm_pad / 4]
+  const int4* hex_desc;    // 6-trial group descriptors [ceil(n_dm / 6)][C], or null
   int32_t C;
   int32_t n_dm;
   int32_t n_dm_pad;
@@ -96,6 +95,9 @@ int batch_blocks_per_sm(dd_dtype dtype, int smem);
 cudaError_t launch_batch(dd_dtype dtype, const BatchBeam* beams, const BatchItem* items, int n_items, int* counter,
                          int* status, int smem, int grid, cudaStream_t s);
 
+// TMW6 needs 16-byte aligned input rows of a multiple of 32 floats (128 bytes).
+bool tmw6_accepts(const void* in, int64_t in_stride);
+
 // Forward launch on a given configuration.
 cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
 
@@ -110,10 +112,9 @@ dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const 
 // Shared-memory limit for one block (opt-in maximum on sm_103a).
 constexpr int kMaxSmemPerBlock = 227 * 1024;
 
-// REGWIN constants: DM trials per warp group and the largest in-group offset
-// the descriptors can carry.
-constexpr int kRwGroup = 8;
-constexpr int kRwMaxOff = 31;
+// TMW6: the largest offset between a 6-trial group's first and last trial
+// that its Tensor Memory windows can hold.
+constexpr int kW6MaxOff = 31;
 
 }  // namespace dd
 
@@ -127,12 +128,12 @@ struct dd_plan_s {
   std::vector<int32_t> delays;        // host copy [n_dm][C]
   int32_t* d_delays = nullptr;        // [n_dm][C]
   int32_t* d_delaysT = nullptr;       // [C][n_dm_pad]
-  int4* d_regwin_desc = nullptr;      // [C][n_dm_pad / 8]
-  int4* d_quad_desc = nullptr;        // [C][n_dm_pad / 4]
+  int4* d_hex_desc = nullptr;         // [ceil(n_dm / 6)][C], float plans whose offsets fit a window
   int* d_status = nullptr;            // device error word
   int64_t device_bytes = 0;
   std::vector<dd::TileConfig> configs;
   int selected = 0;
+  int fallback = 0;                   // staged configuration for inputs the selected one cannot take
   // host-buffer forward staging (allocated on first dd_forward_host)
   void* h_dev_in = nullptr;
   void* h_dev_out = nullptr;

@@ -14,13 +14,10 @@
 namespace dd {
 
 std::vector<TileConfig> staged_menu(dd_dtype dtype);
-std::vector<TileConfig> regwin_menu(dd_dtype dtype);
-std::vector<TileConfig> tmrw_menu(dd_dtype dtype);
 std::vector<TileConfig> u8pk_menu(dd_dtype dtype);
+std::vector<TileConfig> tmw6_menu(dd_dtype dtype);
 int u8pk_smem_for(const TileConfig& cfg, int pitch);
-int tmrw_smem_for(const TileConfig& cfg, int pitch);
 int staged_smem_for(dd_dtype dtype, int stages, int cc, int bd, int pitch);
-int regwin_smem_for(dd_dtype dtype, const TileConfig& cfg, int pitch);
 
 // Eq. 1 (Section 2): delay in seconds of channel frequency f relative to the
 // top of the band f_h is 4150 * DM * (1/f^2 - 1/f_h^2) (MHz); divided by the
@@ -61,30 +58,30 @@ static int32_t block_spread(const dd_plan_s& p, int bd) {
   return best;
 }
 
-// Descriptor of (channel c, group of `gs` trials starting at g*gs), gs = 8 or 4:
-// x = delay of the group's first trial; y (and z for gs = 8) = the trials'
-// offsets relative to it, one byte each, trials 0..3 (4..7); w = the largest
-// offset (the group's last trial).  Returns the largest offset seen; trials
-// past n_dm repeat the last one.
-static int32_t build_group_desc(const dd_plan_s& p, std::vector<int4>& desc, int32_t n_groups, int gs) {
-  desc.assign((size_t)p.C * n_groups, int4{0, 0, 0, 0});
+// Descriptor of (channel c, group of 6 trials starting at 6g), stored
+// group-major ([g][c]: a block reads consecutive entries), for windows
+// aligned down to 4 floats: x = delay of the group's first trial; y, z = the
+// column of each trial's first sample in the window, (x & 3) + offset, one
+// byte each (trials 0..3 in y, 4..5 in z); w = window width in floats,
+// (x & 3) + 32 + the largest offset.  Returns the largest offset seen.
+static int32_t build_hex_desc(const dd_plan_s& p, std::vector<int4>& desc) {
+  const int32_t n_g = (p.n_dm + 5) / 6;
+  desc.assign((size_t)p.C * n_g, int4{0, 0, 0, 0});
   int32_t worst = 0;
   for (int32_t c = 0; c < p.C; ++c) {
-    for (int32_t g = 0; g < n_groups; ++g) {
-      const int32_t i0 = std::min(g * gs, p.n_dm - 1);
-      const int32_t base = p.delays[(size_t)i0 * p.C + c];
+    for (int32_t g = 0; g < n_g; ++g) {
+      const int32_t base = p.delays[(size_t)(6 * g) * p.C + c];
+      const int32_t sh = base & 3;
       uint32_t packed[2] = {0, 0};
       int32_t mx = 0;
-      for (int j = 0; j < gs; ++j) {
-        const int32_t i = std::min(g * gs + j, p.n_dm - 1);
+      for (int j = 0; j < 6; ++j) {
+        const int32_t i = std::min(6 * g + j, p.n_dm - 1);
         const int32_t o = p.delays[(size_t)i * p.C + c] - base;
         mx = std::max(mx, o);
-        const uint32_t ob = (uint32_t)std::min(o, 255);
-        packed[j / 4] |= ob << (8 * (j % 4));
+        packed[j / 4] |= (uint32_t)std::min(sh + o, 255) << (8 * (j % 4));
       }
       worst = std::max(worst, mx);
-      desc[(size_t)c * n_groups + g] =
-          gs == 8 ? int4{base, (int)packed[0], (int)packed[1], mx} : int4{base, (int)packed[0], mx, 0};
+      desc[(size_t)g * p.C + c] = int4{base, (int)packed[0], (int)packed[1], sh + 32 + mx};
     }
   }
   return worst;
@@ -95,8 +92,7 @@ int32_t block_spread_of(const dd_plan_s& p, int bd) { return block_spread(p, bd)
 void free_plan_device(dd_plan_s* p) {
   cudaFree(p->d_delays);
   cudaFree(p->d_delaysT);
-  cudaFree(p->d_regwin_desc);
-  cudaFree(p->d_quad_desc);
+  cudaFree(p->d_hex_desc);
   cudaFree(p->d_status);
   cudaFree(p->h_dev_in);
   cudaFree(p->h_dev_out);
@@ -109,28 +105,39 @@ void free_plan_device(dd_plan_s* p) {
     p->adj = nullptr;
   }
   p->d_delays = p->d_delaysT = nullptr;
-  p->d_regwin_desc = nullptr;
-  p->d_quad_desc = nullptr;
+  p->d_hex_desc = nullptr;
   p->d_status = nullptr;
   p->h_dev_in = p->h_dev_out = nullptr;
   p->h_dev_w = nullptr;
   p->adj_pad = p->adj_g = nullptr;
 }
 
-// Default configuration: the first valid entry of a preference list chosen by
-// the shape of the problem; dd_tune replaces it with a measured choice.
-static int default_config(const dd_plan_s& p) {
-  // measured fastest on the Apertif setup first (f32: 5.2 ms, u8: 4.2 ms)
-  const char* prefs_f32[] = {"staged_d8_t1024_c4_s3", "staged_d16_t512_c8_s3", "staged_d8_t512_c8_s3",
-                             "staged_d16_t256_c8_s3", "naive_t256"};
-  const char* prefs_u8[] = {"u8pk_w8x1_d2_c16_st4", "u8pk_w8x1_d4_c16_st3", "staged_d8_t1024_c4_s3",
-                            "staged_d16_t512_c8_s3", "naive_t256"};
-  const char** prefs = p.dtype == DD_U8_I32 ? prefs_u8 : prefs_f32;
-  for (int k = 0; k < 5; ++k)
+// Default configuration: the first valid entry of a preference list, in
+// the order measured on the Table 2 setups (Apertif float: TMW6 5.06 ms,
+// staged d32/t512 5.66 ms; LOFAR float: staged d32/t512 3.76 ms; Apertif
+// uint8: U8PK 4.25 ms); dd_tune replaces it with a measured choice.  TMW6 is
+// offered only where a 6-trial group's offsets fit its windows (Apertif, not
+// LOFAR).
+static const char* const kPrefsF32[] = {"tmw6_f32_d6_t4096", "staged_d32_t512_c4_s3", "staged_d8_t1024_c4_s3",
+                                        "staged_d16_t512_c8_s3", "staged_d16_t256_c8_s3", "naive_t256"};
+static const char* const kPrefsU8[] = {"u8pk_w8x1_d2_c16_st4", "u8pk_w8x1_d4_c16_st3", "staged_d8_t1024_c4_s3",
+                                       "staged_d16_t512_c8_s3", "naive_t256"};
+
+static int preferred(const dd_plan_s& p, bool staged_only) {
+  const bool u8 = p.dtype == DD_U8_I32;
+  const char* const* prefs = u8 ? kPrefsU8 : kPrefsF32;
+  const size_t n = u8 ? sizeof(kPrefsU8) / sizeof(kPrefsU8[0]) : sizeof(kPrefsF32) / sizeof(kPrefsF32[0]);
+  for (size_t k = 0; k < n; ++k)
     for (size_t j = 0; j < p.configs.size(); ++j)
-      if (p.configs[j].name == prefs[k]) return (int)j;
+      if (p.configs[j].name == prefs[k] && (!staged_only || p.configs[j].kind == Kind::Staged)) return (int)j;
+  for (size_t j = 0; j < p.configs.size(); ++j)
+    if (!staged_only || p.configs[j].kind == Kind::Staged) return (int)j;
   return 0;
 }
+static int default_config(const dd_plan_s& p) { return preferred(p, false); }
+// The configuration used when the selected one cannot take an input's
+// layout (TMW6 needs 128-byte rows): the preferred shared-memory kernel.
+static int fallback_config(const dd_plan_s& p) { return preferred(p, true); }
 
 // Everything a plan derives from its delay table (p->delays [n_dm][C], rows
 // non-decreasing along the trial index for every channel): sizes, device
@@ -146,29 +153,36 @@ dd_status finish_plan(dd_plan_s* p) {
   for (int32_t c = 0; c < p->C; ++c)
     for (int32_t i = 0; i < p->n_dm_pad; ++i)
       dT[(size_t)c * p->n_dm_pad + i] = p->delays[(size_t)std::min(i, p->n_dm - 1) * p->C + c];
-  const int32_t n_groups = p->n_dm_pad / kRwGroup;
-  std::vector<int4> desc, desc4;
-  const int32_t rw_worst = build_group_desc(*p, desc, n_groups, kRwGroup);
-  (void)build_group_desc(*p, desc4, p->n_dm_pad / 4, 4);
-
-  const size_t bytes_d = p->delays.size() * 4, bytes_dT = dT.size() * 4, bytes_desc = desc.size() * sizeof(int4);
-  const size_t bytes_desc4 = desc4.size() * sizeof(int4);
+  const size_t bytes_d = p->delays.size() * 4, bytes_dT = dT.size() * 4;
   cudaError_t e = cudaMalloc(&p->d_delays, bytes_d);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_delaysT, bytes_dT);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_regwin_desc, bytes_desc);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_quad_desc, bytes_desc4);
-  if (e == cudaSuccess) e = cudaMemcpy(p->d_quad_desc, desc4.data(), bytes_desc4, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
   if (e == cudaSuccess) e = cudaMemcpy(p->d_delays, p->delays.data(), bytes_d, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(p->d_delaysT, dT.data(), bytes_dT, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(p->d_regwin_desc, desc.data(), bytes_desc, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p->d_status, 0, sizeof(int));
   if (e != cudaSuccess) {
     free_plan_device(p);
     return e == cudaErrorMemoryAllocation ? set_error(DD_ERR_NOMEM, "dd_plan: device allocation failed")
                                           : set_cuda_error("dd_plan: upload", e);
   }
-  p->device_bytes = (int64_t)(bytes_d + bytes_dT + bytes_desc + bytes_desc4 + sizeof(int));
+  p->device_bytes = (int64_t)(bytes_d + bytes_dT + sizeof(int));
+  // 6-trial descriptors, only where the windows fit (float plans, offsets <= 31)
+  bool hex_ok = false;
+  if (p->dtype == DD_F32_F32) {
+    std::vector<int4> desc6;
+    if (build_hex_desc(*p, desc6) <= kW6MaxOff) {
+      const size_t bytes6 = desc6.size() * sizeof(int4);
+      e = cudaMalloc(&p->d_hex_desc, bytes6);
+      if (e == cudaSuccess) e = cudaMemcpy(p->d_hex_desc, desc6.data(), bytes6, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        free_plan_device(p);
+        return e == cudaErrorMemoryAllocation ? set_error(DD_ERR_NOMEM, "dd_plan: device allocation failed")
+                                              : set_cuda_error("dd_plan: upload", e);
+      }
+      p->device_bytes += (int64_t)bytes6;
+      hex_ok = true;
+    }
+  }
 
   // configuration menu, filtered by what this geometry allows
   const int V = p->dtype == DD_U8_I32 ? 16 : 4;
@@ -195,27 +209,14 @@ dd_status finish_plan(dd_plan_s* p) {
     if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
     p->configs.push_back(cfg);
   }
-  if (rw_worst <= kRwMaxOff) {
-    for (TileConfig cfg : regwin_menu(p->dtype)) {
-      const int64_t spread = block_spread(*p, cfg.bd);
-      const int64_t pitch = (cfg.bt + spread + 2 * V + V - 1) / V * V + (p->dtype == DD_U8_I32 ? 0 : 0);
-      cfg.pitch = (int)pitch;
-      cfg.smem = regwin_smem_for(p->dtype, cfg, cfg.pitch);
-      if (cfg.smem > kMaxSmemPerBlock) continue;
-      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
-      p->configs.push_back(cfg);
-    }
-    for (TileConfig cfg : tmrw_menu(p->dtype)) {
-      const int64_t spread = block_spread(*p, cfg.bd);
-      // + 32: window loads run in blocks of 8 and may read past the window
-      cfg.pitch = (int)((cfg.bt + spread + 2 * V + 32 + V - 1) / V * V);
-      cfg.smem = tmrw_smem_for(cfg, cfg.pitch);
-      if (cfg.smem > kMaxSmemPerBlock) continue;
+  if (hex_ok) {
+    for (TileConfig cfg : tmw6_menu(p->dtype)) {
       if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
       p->configs.push_back(cfg);
     }
   }
   p->selected = default_config(*p);
+  p->fallback = fallback_config(*p);
   return DD_OK;
 }
 

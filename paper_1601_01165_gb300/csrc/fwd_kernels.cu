@@ -517,8 +517,7 @@ static cudaError_t launch_staged(const TileConfig& cfg, const FwdArgs& a, cudaSt
   return cudaErrorInvalidConfiguration;
 }
 
-cudaError_t launch_regwin(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
-cudaError_t launch_tmrw(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_tmw6(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
 
 cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s) {
   const bool weighted = a.w != nullptr;
@@ -529,10 +528,8 @@ cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs&
     case Kind::Staged:
       if (dtype == DD_U8_I32) return launch_staged<uint8_t, false>(cfg, a, s);
       return weighted ? launch_staged<float, true>(cfg, a, s) : launch_staged<float, false>(cfg, a, s);
-    case Kind::RegWin:
-      return launch_regwin(cfg, dtype, a, s);
-    case Kind::TmRw:
-      return launch_tmrw(cfg, dtype, a, s);
+    case Kind::TmW6:
+      return launch_tmw6(cfg, dtype, a, s);
     case Kind::U8Pk:
       if (dtype != DD_U8_I32 || weighted) return cudaErrorInvalidConfiguration;
       return launch_u8pk(cfg, a, s);

@@ -1,0 +1,369 @@
+// TMW6 forward kernel (float32): 6 DM trials x 4096 samples per block, input
+// windows shared through Tensor Memory, one batched TMEM read per channel.
+//
+// Section 2 notes that nearby DM trials read nearly the same input samples;
+// Section 2.2 exploits it by sharing staged input within a work group.  Here
+// the sharing happens in Tensor Memory, which a warp can read at a run-time
+// column address (registers cannot be indexed at run time) and at ~3.5x the
+// shared-memory bandwidth:
+//
+//  * TMEM lane r holds, per channel, the window of the input that lane r's 32
+//    output samples need for all 6 trials: 32 + max offset columns, aligned
+//    down to 4 floats.  Windows live in a ring of 7 slots of 68 columns.
+//  * 12 warps, 3 per TMEM lane quadrant (warp w serves lanes 32 (w % 4) ..,
+//    which is also its SM sub-partition); warp p = w / 4 owns trials 2p and
+//    2p + 1.  Each channel it issues two 32-column loads at column shift + o_j
+//    (o_j = delay(c, i0 + j) - delay(c, i0)) and waits once; 64 adds follow.
+//  * Warp p of a quadrant writes the quadrant's windows of channels c = p
+//    (mod 3), three channels ahead, while its own TMEM loads are in flight.
+//    The input comes from its private stages: a 3-D TMA load (128-byte
+//    swizzle) of the quadrant's 35 rows of 32 samples from the row holding
+//    t0 + delay(c, i0), plus the channel's 16-byte descriptor (base delay,
+//    column bytes, window width); 16-byte shared loads read the swizzled rows
+//    without bank conflicts.  Once a window is out, the warp reloads the
+//    stage with its channel nine later, so quadrants never wait on each other.
+//
+// mbarriers: stage full (TMA bytes), window full (the writer), window empty
+// (the quadrant's three readers).  Every wait is bounded; a timeout sets the
+// status word and ends the block.  Sums run in channel order as in every
+// kernel here, so results are bit-identical to theirs.  The 6 x 4096 sums
+// leave through a swizzled shared-memory tile with coalesced 16-byte stores.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <mutex>
+
+#include "dd_internal.h"
+#include "ptx.cuh"
+
+namespace dd {
+
+namespace {
+
+constexpr int kT = 6;                       // DM trials per block
+constexpr int kQRows = 35;                  // tile rows of 32 samples per quadrant (32 lanes + 3)
+constexpr int kTileBytes = kQRows * 128;    // 4480
+constexpr int kStage = 5 * 1024;            // tile + descriptor, whole 1024-byte swizzle atoms
+constexpr int kWS = 3;                      // stages per warp (its channels c, c + 3, c + 6 in flight)
+constexpr int kSlot = 68;                   // columns per window: shift (<= 3) + 32 + offset (<= 31), 4-aligned
+constexpr int kLead = 3;                    // warps per quadrant = channels per step
+constexpr int kAhead = kLead * kWS;         // a warp's tile loads run this many channels ahead
+constexpr int kBT = 128 * 32;               // samples per block
+constexpr int kThreads = 384;
+constexpr int kHdr = 2048;
+constexpr int kNStages = 12 * kWS;
+constexpr int kSmem = kHdr + kNStages * kStage + 1024;  // + slack to align the stages to 1024 bytes
+constexpr uint32_t kCols = 512;
+static_assert(2 * 3 * kSlot <= (int)kCols, "two sets of three windows fit TMEM");
+static_assert(kTileBytes + 16 <= kStage, "stage holds tile and descriptor");
+static_assert(kT * kBT * 4 <= kNStages * kStage, "output tile fits the stage area");
+
+struct Hdr {
+  uint64_t sfull[12][kWS];   // per warp: its stages
+  int4 slot[4][2 * kLead];   // per quadrant window slot: column bytes (2 words), weight bits
+  uint32_t tbase;
+  int failed;
+};
+static_assert(sizeof(Hdr) <= kHdr, "header fits");
+
+// 16 bytes at 4-float chunk `e4` of row `r` of a 128B-swizzled tile.  A plain
+// load, so the compiler may schedule the next piece's loads ahead of the
+// previous piece's TMEM store (the stores below do not clobber memory).
+__device__ __forceinline__ float4 tile_chunk(const unsigned char* tile, int r, int e4) {
+  const int row = r + (e4 >> 3);
+  return *reinterpret_cast<const float4*>(tile + row * 128 + (((e4 & 7) ^ (row & 7)) << 4));
+}
+
+__device__ __forceinline__ void ld_chunks4(const unsigned char* tile, int r, int e4, float* v) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float4 x = tile_chunk(tile, r, e4 + k);
+    v[4 * k] = x.x, v[4 * k + 1] = x.y, v[4 * k + 2] = x.z, v[4 * k + 3] = x.w;
+  }
+}
+
+// TMEM stores that read registers only: ordered with the other tcgen05
+// instructions (volatile), not with shared-memory accesses.
+__device__ __forceinline__ void st16_regs(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
+      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]));
+}
+__device__ __forceinline__ void st4_regs(uint32_t taddr, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]));
+}
+
+}  // namespace
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_constant__ CUtensorMap tmap, FwdArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Hdr& H = *reinterpret_cast<Hdr*>(smem_raw);
+  unsigned char* stages = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + kHdr + 1023) & ~static_cast<uintptr_t>(1023));
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int q = warp & 3, p = warp >> 2;
+  const int r = 32 * q + lane;  // TMEM lane of this thread
+  const int64_t t0 = (int64_t)blockIdx.x * kBT;
+  const int g = blockIdx.y;
+  const int i0 = g * kT;
+  const int C = a.C;
+  const int4* gdesc = a.hex_desc + (int64_t)g * C;  // this block's descriptors, one per channel
+
+  if (tid == 0) {
+    for (int w = 0; w < 12; ++w)
+      for (int j = 0; j < kWS; ++j) mbar_init(&H.sfull[w][j], 1);
+    H.failed = 0;
+    fence_mbar_init();
+  }
+  if (warp == 0) tmem_alloc(&H.tbase, kCols);
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  const uint32_t tq = H.tbase + ((uint32_t)(32 * q) << 16);  // this quadrant's lanes, column 0
+
+  // ------------------------------------------------ this warp's tile loads
+  // Warp (q, p) writes the windows of channels c = p (mod 3) for quadrant q.
+  // Its m-th channel (c = p + 3m) sits in its stage m % kWS; lane 0 loads the
+  // quadrant's 35 rows of the tile and the channel's descriptor there, and
+  // reloads the stage with channel c + 9 once the window is out.
+  unsigned char* my_stages = stages + (size_t)warp * kWS * kStage;
+  int issued = 0;  // own channels whose load was issued (lane 0)
+  auto base_of = [&](int c) { return c < C ? __ldg(&gdesc[c].x) : 0; };
+  auto issue = [&](int c, int base) {
+    const int m = (c - p) / kLead, j = m % kWS;
+    unsigned char* st = my_stages + (size_t)j * kStage;
+    mbar_arrive_expect_tx(&H.sfull[warp][j], kTileBytes + 16);
+    bulk_g2s(st + kTileBytes, gdesc + c, 16, &H.sfull[warp][j]);
+    tma_load_3d(st, &tmap, 0, (int)((t0 + base) >> 5) + 32 * q, c, &H.sfull[warp][j]);
+  };
+  int nbase = 0;  // base delay of this warp's next channel to load (lane 0)
+  if (lane == 0) {
+    int b0[kWS];
+#pragma unroll
+    for (int j = 0; j < kWS; ++j) b0[j] = base_of(p + kLead * j);
+#pragma unroll
+    for (int j = 0; j < kWS; ++j)
+      if (p + kLead * j < C) {
+        issue(p + kLead * j, b0[j]);
+        ++issued;
+      }
+    nbase = base_of(p + kAhead);
+  }
+
+  // ------------------------------------------ window writer (one channel)
+  // Copies the window of channel c (c = p mod 3) from this warp's stage into
+  // TMEM slot `sl` of the quadrant and reloads the stage; false on a timeout
+  // (the window is then left unwritten and the block reports the error).
+  auto write_window = [&](int c, int sl) -> bool {
+    const int m = (c - p) / kLead, j = m % kWS;
+    if (!__all_sync(0xffffffffu, mbar_wait_bounded(&H.sfull[warp][j], (uint32_t)((m / kWS) & 1), kWaitLimitCycles)))
+      return false;
+    unsigned char* st = my_stages + (size_t)j * kStage;
+    const int4 dsc = *reinterpret_cast<const int4*>(st + kTileBytes);
+    const int c4 = (int)((t0 + dsc.x) & 31) >> 2;
+    const int need = dsc.w;  // floats from the aligned start: shift + 32 + max offset
+    const uint32_t col = tq + (uint32_t)(kSlot * sl);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if (16 * k < need) {
+        float v[16];
+        ld_chunks4(st, lane, c4 + 4 * k, v);
+        st16_regs(col + 16 * k, v);
+      }
+    }
+    if (need > 64) {
+      const float4 x = tile_chunk(st, lane, c4 + 16);
+      const float v[4] = {x.x, x.y, x.z, x.w};
+      st4_regs(col + 64, v);
+    }
+    float wc = 1.0f;
+    if constexpr (WEIGHTED) wc = __ldg(a.w + c);
+    __syncwarp();
+    if (lane == 0) {
+      H.slot[q][sl] = make_int4(dsc.y, dsc.z, __float_as_int(wc), 0);
+      // the stage is read: reload it with this warp's channel kAhead later
+      // (the window's shared loads have completed: the TMEM stores consumed them)
+      if (c + kAhead < C) {
+        issue(c + kAhead, nbase);
+        ++issued;
+        nbase = base_of(c + kAhead + kLead);
+      }
+    }
+    return true;
+  };
+  // The quadrant's three warps meet at a named barrier once per step of three
+  // channels.  Every warp runs the same number of steps whatever happens
+  // (a timeout only skips work), so each barrier is always completed.
+  const uint32_t bar_id = 1 + (uint32_t)q;
+  auto quad_sync = [&]() {
+    tmem_wait_st();
+    tmem_fence_before_sync();
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(96) : "memory");
+    tmem_fence_after_sync();
+  };
+
+  bool ok = true;
+  if (p < C) ok = write_window(p, p);  // step 0's windows go to slots 0..2
+  quad_sync();
+
+  // ------------------------------------------------------------ main loop
+  float acc[2][32];
+#pragma unroll
+  for (int jj = 0; jj < 2; ++jj)
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[jj][k] = 0.0f;
+  const int shift_a = 16 * (p & 1), word_a = p >> 1;  // where trial 2p's column byte sits
+  const int n_steps = (C + kLead - 1) / kLead;
+  for (int n = 0; n < n_steps; ++n) {
+    const int set = (n & 1) * kLead;  // slots of this step's windows
+#pragma unroll
+    for (int k = 0; k < kLead; ++k) {
+      const int c = kLead * n + k;
+      if (c >= C) break;  // the same for every warp
+      const int4 si = H.slot[q][set + k];
+      const uint32_t bytes = (uint32_t)(word_a ? si.y : si.x) >> shift_a;
+      const uint32_t col = tq + (uint32_t)(kSlot * (set + k));
+      float v0[32], v1[32];
+      tmem_ld32(col + (bytes & 0xffu), v0);
+      tmem_ld32(col + ((bytes >> 8) & 0xffu), v1);
+      // while the first loads are in flight: this warp's window of the next step
+      if (k == 0 && ok) {
+        const int cn = kLead * (n + 1) + p;
+        if (cn < C) ok = write_window(cn, (kLead - set) + p);
+      }
+      tmem_wait_ld();
+      if constexpr (WEIGHTED) {
+        const float wc = __int_as_float(si.z);
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          acc[0][u] = fmaf(wc, v0[u], acc[0][u]);
+          acc[1][u] = fmaf(wc, v1[u], acc[1][u]);
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          acc[0][u] += v0[u];
+          acc[1][u] += v1[u];
+        }
+      }
+    }
+    quad_sync();  // next step's windows written; this step's slots free
+  }
+  if (!ok && lane == 0) {
+    report_error(a.status, kDevWaitTimeout);
+    atomicExch(&H.failed, 1);
+  }
+  tmem_wait_st();
+  tmem_wait_ld();
+  // no TMA may still be landing when the stage area is reused or the block
+  // leaves (after a timeout some loads may not have been consumed)
+  if (lane == 0) {
+    for (int m = max(0, issued - kWS); m < issued; ++m)
+      (void)mbar_wait_bounded(&H.sfull[warp][m % kWS], (uint32_t)((m / kWS) & 1), kWaitLimitCycles);
+  }
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(H.tbase, kCols);
+  if (H.failed) return;
+
+  // ------------------------------------------------------------ epilogue
+  // trial-major tile of 16-byte chunks; chunk k4 of row r sits at k4 ^ (r & 7)
+  float4* ot = reinterpret_cast<float4*>(stages);
+#pragma unroll
+  for (int jj = 0; jj < 2; ++jj) {
+    float4* row = ot + (size_t)(2 * p + jj) * (kBT / 4) + r * 8;
+#pragma unroll
+    for (int k4 = 0; k4 < 8; ++k4)
+      row[k4 ^ (r & 7)] = make_float4(acc[jj][4 * k4], acc[jj][4 * k4 + 1], acc[jj][4 * k4 + 2], acc[jj][4 * k4 + 3]);
+  }
+  __syncthreads();
+  float* __restrict__ out = static_cast<float*>(a.out);
+  const bool vec = (reinterpret_cast<uintptr_t>(out) % 16 == 0) && (a.out_stride % 4 == 0);
+  for (int u = tid; u < kT * (kBT / 4); u += kThreads) {
+    const int j = u / (kBT / 4), m = u % (kBT / 4);
+    const int i = i0 + j;
+    if (i >= a.n_dm) break;  // u grows with j
+    const int rr = m >> 3, k4 = m & 7;
+    const float4 x = ot[(size_t)j * (kBT / 4) + rr * 8 + (k4 ^ (rr & 7))];
+    const int64_t t = t0 + 4 * m;
+    float* o = out + (int64_t)i * a.out_stride + t;
+    if (vec && t + 3 < a.n_out) {
+      *reinterpret_cast<float4*>(o) = x;
+    } else {
+      if (t < a.n_out) o[0] = x.x;
+      if (t + 1 < a.n_out) o[1] = x.y;
+      if (t + 2 < a.n_out) o[2] = x.z;
+      if (t + 3 < a.n_out) o[3] = x.w;
+    }
+  }
+}
+
+// ------------------------------------------------------------------- launch
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder, looked up once through the runtime.
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+bool tmw6_accepts(const void* in, int64_t in_stride) {
+  return in_stride % 32 == 0 && (reinterpret_cast<uintptr_t>(in) % 16) == 0 && encode_fn() != nullptr;
+}
+
+// Tensor map over the float input viewed as [C][in_stride / 32 rows][32]: one
+// load brings `rows` consecutive 128-byte rows of one channel, stored with
+// the 128-byte swizzle; rows past the end read as zero.
+static bool encode_row_tiles(CUtensorMap* tm, const FwdArgs& a, int rows) {
+  const cuuint64_t dims[3] = {32, (cuuint64_t)(a.in_stride / 32), (cuuint64_t)a.C};
+  const cuuint64_t strides[2] = {128, (cuuint64_t)a.in_stride * 4};
+  const cuuint32_t box[3] = {32, (cuuint32_t)rows, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(a.in), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+cudaError_t launch_tmw6(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s) {
+  (void)cfg;
+  if (dtype != DD_F32_F32 || !tmw6_accepts(a.in, a.in_stride) || a.hex_desc == nullptr)
+    return cudaErrorInvalidConfiguration;
+  CUtensorMap tm;
+  if (!encode_row_tiles(&tm, a, kQRows)) return cudaErrorInvalidValue;
+  auto kern = a.w ? fwd_tmw6_kernel<true> : fwd_tmw6_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((a.n_out + kBT - 1) / kBT), (unsigned)((a.n_dm + kT - 1) / kT));
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  kern<<<grid, kThreads, kSmem, s>>>(tm, a);
+  return cudaGetLastError();
+}
+
+std::vector<TileConfig> tmw6_menu(dd_dtype dtype) {
+  std::vector<TileConfig> v;
+  if (dtype != DD_F32_F32) return v;
+  v.push_back({Kind::TmW6, kT, kBT, 1, kWS, kThreads, 32, kSmem, 0, "tmw6_f32_d6_t4096"});
+  return v;
+}
+
+}  // namespace dd

@@ -73,7 +73,7 @@ extern "C" dd_status dd_tune(dd_plan_t plan, double budget_s, const char* db_pat
     }
   }
   const int elem = plan->dtype == DD_U8_I32 ? 1 : 4;
-  const int64_t v = 16 / elem;
+  const int64_t v = 128 / elem;  // 128-byte rows: every configuration takes the input
   const int64_t stride = (plan->n_in + v - 1) / v * v;
   void* in = nullptr;
   void* out = nullptr;
