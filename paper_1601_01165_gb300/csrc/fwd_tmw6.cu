@@ -46,7 +46,7 @@ constexpr int kQRows = 35;                  // tile rows of 32 samples per quadr
 constexpr int kTileBytes = kQRows * 128;    // 4480
 constexpr int kStage = 5 * 1024;            // tile + descriptor, whole 1024-byte swizzle atoms
 constexpr int kWS = 3;                      // stages per warp (its channels c, c + 3, c + 6 in flight)
-constexpr int kSlot = 68;                   // columns per window: shift (<= 3) + 32 + offset (<= 31), 4-aligned
+constexpr int kSlot = 80;                   // columns per window: 5 groups of 16 (see the window writer)
 constexpr int kLead = 3;                    // warps per quadrant = channels per step
 constexpr int kAhead = kLead * kWS;         // a warp's tile loads run this many channels ahead
 constexpr int kBT = 128 * 32;               // samples per block
@@ -56,6 +56,7 @@ constexpr int kNStages = 12 * kWS;
 constexpr int kSmem = kHdr + kNStages * kStage + 1024;  // + slack to align the stages to 1024 bytes
 constexpr uint32_t kCols = 512;
 static_assert(2 * 3 * kSlot <= (int)kCols, "two sets of three windows fit TMEM");
+static_assert(12 + 3 + 32 + kW6MaxOff <= kSlot - 1, "a trial's last column stays inside its window");
 static_assert(kTileBytes + 16 <= kStage, "stage holds tile and descriptor");
 static_assert(kT * kBT * 4 <= kNStages * kStage, "output tile fits the stage area");
 
@@ -67,18 +68,17 @@ struct Hdr {
 };
 static_assert(sizeof(Hdr) <= kHdr, "header fits");
 
-// 16 bytes at 4-float chunk `e4` of row `r` of a 128B-swizzled tile.  A plain
-// load, so the compiler may schedule the next piece's loads ahead of the
-// previous piece's TMEM store (the stores below do not clobber memory).
-__device__ __forceinline__ float4 tile_chunk(const unsigned char* tile, int r, int e4) {
-  const int row = r + (e4 >> 3);
-  return *reinterpret_cast<const float4*>(tile + row * 128 + (((e4 & 7) ^ (row & 7)) << 4));
-}
+// Rows of a tile written by a 128B-swizzled TMA load (tile base 1024-byte
+// aligned): 16-byte chunk x (0..7) of row y sits at y * 128 + ((x ^ y) & 7) * 16,
+// which is rbase(y) ^ (x << 4) with rbase(y) = y * 128 + ((y & 7) << 4).
+__device__ __forceinline__ uint32_t rbase(int y) { return (uint32_t)y * 128u + ((uint32_t)(y & 7) << 4); }
 
-__device__ __forceinline__ void ld_chunks4(const unsigned char* tile, int r, int e4, float* v) {
+// Four consecutive chunks of one row (compile-time chunk index X0..X0+3).
+template <int X0>
+__device__ __forceinline__ void ld_group(const unsigned char* tile, uint32_t rb, float* v) {
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const float4 x = tile_chunk(tile, r, e4 + k);
+    const float4 x = *reinterpret_cast<const float4*>(tile + (rb ^ (uint32_t)((X0 + k) << 4)));
     v[4 * k] = x.x, v[4 * k + 1] = x.y, v[4 * k + 2] = x.z, v[4 * k + 3] = x.w;
   }
 }
@@ -91,10 +91,6 @@ __device__ __forceinline__ void st16_regs(uint32_t taddr, const float* v) {
           taddr),
       "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
       "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]));
-}
-__device__ __forceinline__ void st4_regs(uint32_t taddr, const float* v) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "f"(v[0]), "f"(v[1]),
-               "f"(v[2]), "f"(v[3]));
 }
 
 }  // namespace
@@ -166,27 +162,36 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
       return false;
     unsigned char* st = my_stages + (size_t)j * kStage;
     const int4 dsc = *reinterpret_cast<const int4*>(st + kTileBytes);
+    // The window is the 16-float groups of rows lane .. lane + 2 (96 floats)
+    // that hold elements [4 c4, 4 c4 + need): groups G0 = c4 / 4 .. G0 + ng - 1,
+    // stored from the slot's first column, so element 4 c4 + x lands on column
+    // 4 (c4 % 4) + x.  G0 is 0 or 1: both cases use compile-time chunk indices.
     const int c4 = (int)((t0 + dsc.x) & 31) >> 2;
     const int need = dsc.w;  // floats from the aligned start: shift + 32 + max offset
+    const int lead = 4 * (c4 & 3);
+    const int ng = (lead + need + 15) >> 4;  // 3..5
     const uint32_t col = tq + (uint32_t)(kSlot * sl);
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (16 * k < need) {
-        float v[16];
-        ld_chunks4(st, lane, c4 + 4 * k, v);
-        st16_regs(col + 16 * k, v);
-      }
-    }
-    if (need > 64) {
-      const float4 x = tile_chunk(st, lane, c4 + 16);
-      const float v[4] = {x.x, x.y, x.z, x.w};
-      st4_regs(col + 64, v);
+    const uint32_t rb0 = rbase(lane), rb1 = rbase(lane + 1), rb2 = rbase(lane + 2);
+    float v[16];
+    if (c4 < 4) {  // groups 0..4: row lane (0, 1), row lane + 1 (2, 3), row lane + 2 (4)
+      ld_group<0>(st, rb0, v), st16_regs(col, v);
+      ld_group<4>(st, rb0, v), st16_regs(col + 16, v);
+      ld_group<0>(st, rb1, v), st16_regs(col + 32, v);
+      if (ng > 3) ld_group<4>(st, rb1, v), st16_regs(col + 48, v);
+      if (ng > 4) ld_group<0>(st, rb2, v), st16_regs(col + 64, v);
+    } else {  // groups 1..5
+      ld_group<4>(st, rb0, v), st16_regs(col, v);
+      ld_group<0>(st, rb1, v), st16_regs(col + 16, v);
+      ld_group<4>(st, rb1, v), st16_regs(col + 32, v);
+      if (ng > 3) ld_group<0>(st, rb2, v), st16_regs(col + 48, v);
+      if (ng > 4) ld_group<4>(st, rb2, v), st16_regs(col + 64, v);
     }
     float wc = 1.0f;
     if constexpr (WEIGHTED) wc = __ldg(a.w + c);
     __syncwarp();
     if (lane == 0) {
-      H.slot[q][sl] = make_int4(dsc.y, dsc.z, __float_as_int(wc), 0);
+      // column bytes of the 6 trials, moved by the window's lead (bytes stay < 256)
+      H.slot[q][sl] = make_int4(dsc.y + lead * 0x01010101, dsc.z + lead * 0x0101, __float_as_int(wc), 0);
       // the stage is read: reload it with this warp's channel kAhead later
       // (the window's shared loads have completed: the TMEM stores consumed them)
       if (c + kAhead < C) {
