@@ -211,7 +211,7 @@ dd_status finish_plan(dd_plan_s* p) {
   }
   if (hex_ok) {
     for (TileConfig cfg : tmw6_menu(p->dtype)) {
-      if ((p->n_dm + cfg.bd - 1) / cfg.bd > 65535) continue;
+      if ((p->n_out + cfg.bt - 1) / cfg.bt > 65535) continue;  // time tiles are the grid's y
       p->configs.push_back(cfg);
     }
   }

@@ -105,8 +105,10 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = warp & 3, p = warp >> 2;
   const int r = 32 * q + lane;  // TMEM lane of this thread
-  const int64_t t0 = (int64_t)blockIdx.x * kBT;
-  const int g = blockIdx.y;
+  // trial groups vary fastest: blocks resident together share one stretch of
+  // the input, which then stays in L2
+  const int64_t t0 = (int64_t)blockIdx.y * kBT;
+  const int g = blockIdx.x;
   const int i0 = g * kT;
   const int C = a.C;
   const int4* gdesc = a.hex_desc + (int64_t)g * C;  // this block's descriptors, one per channel
@@ -358,7 +360,7 @@ cudaError_t launch_tmw6(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a,
   auto kern = a.w ? fwd_tmw6_kernel<true> : fwd_tmw6_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
   if (e != cudaSuccess) return e;
-  dim3 grid((unsigned)((a.n_out + kBT - 1) / kBT), (unsigned)((a.n_dm + kT - 1) / kT));
+  dim3 grid((unsigned)((a.n_dm + kT - 1) / kT), (unsigned)((a.n_out + kBT - 1) / kBT));
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   kern<<<grid, kThreads, kSmem, s>>>(tm, a);
   return cudaGetLastError();
