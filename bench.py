@@ -209,7 +209,7 @@ def run_reference(args, setup):
 
 
 def _config(setup, args, cfg_name, l2_note):
-    return {"workload": f"apertif-like single beam per GPU: {setup.channels} ch from {setup.f_low_mhz} MHz x "
+    return {"workload": f"{setup.name}-like single beam per GPU: {setup.channels} ch from {setup.f_low_mhz} MHz x "
                         f"{setup.chan_bw_mhz} MHz, t_samp {setup.t_samp_s * 1e6:.0f} us, {setup.n_dm} DM trials "
                         f"step {setup.dm_step}, {setup.n_out} output samples",
             "dtype": args.dtype, "kernel_config": cfg_name, "l2": l2_note,
