@@ -246,21 +246,23 @@ dd_status dd_boxcar_snr_noalloc(const float* x, int64_t row_stride, int32_t n_ro
 
 /*
  * Many independent beams (Section 2: each beam is processed independently;
- * Section 5.1: many beams per device) in one persistent kernel launch.
- * dd_batch_create copies the n plans' geometry into one device work list of
- * (beam, DM block, time block) tiles, ordered longest first; the plans must
- * outlive the batch and live on the same device.  Mixed uint8 and float32
- * plans are allowed.
+ * Section 5.1: many beams per device) launched as one CUDA graph.
+ * dd_batch_create orders the n plans longest first and deals them to a few
+ * internal streams by accumulated work (C * n_dm * n_out), so beams too small
+ * to fill the GPU run side by side; the plans must outlive the batch and live
+ * on the same device.  Mixed uint8 and float32 plans are allowed.
  * dd_batch_run: ins[b] / outs[b] are device pointers for beam b with row
- * strides in_strides[b] / out_strides[b] (host arrays of n entries); results
- * are bit-identical to n separate dd_forward calls with the same plans and
- * NULL weights.  The first run on a stream captures the launch into a CUDA
- * graph keyed by the pointer set; later runs with the same pointers replay it
- * (a run on the legacy NULL stream launches without a graph).  Inputs must be
- * 16-byte aligned with 16-byte row pitches (DD_ERR_ALIGN otherwise).  Runs of
- * one batch must not overlap in time (they share the batch's work counters).
- * An expired bounded wait inside the batch kernels is reported in the first
- * plan's device status word (dd_plan_device_status).
+ * strides in_strides[b] / out_strides[b] (host arrays of n entries).  Each
+ * beam runs the forward launch of its own plan's selected configuration with
+ * NULL weights, so results are bit-identical to n separate dd_forward calls.
+ * The first run on a stream records the fork from `stream`, the n launches
+ * and the join into a CUDA graph keyed by the pointer set; later runs with the
+ * same pointers replay it with one launch (a run on the legacy NULL stream
+ * launches directly).  Work queued on `stream` after the run waits for every
+ * beam.  Inputs must be 16-byte aligned with 16-byte row pitches
+ * (DD_ERR_ALIGN otherwise).  Runs of one batch must not overlap in time (they
+ * share the batch's internal streams).  An expired bounded wait in a beam's
+ * kernel is reported in that beam's plan status word (dd_plan_device_status).
  */
 dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, int32_t n);
 dd_status dd_batch_run(dd_batch_t batch, const void* const* ins, const int64_t* in_strides,

@@ -69,7 +69,7 @@ dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const 
     return nullptr;
   };
   if (cfg->kind != Kind::Naive && !aligned) cfg = first_of(Kind::Naive);
-  // TMCP stages 128-byte rows; other layouts take the shared-memory kernel
+  // TMW6 stages 128-byte rows; other layouts take the preferred shared-memory kernel
   if (cfg->kind == Kind::TmW6 && !tmw6_accepts(in, in_stride)) cfg = &p->configs[p->fallback];
   cudaError_t e = launch_forward(*cfg, p->dtype, a, stream);
   if (e != cudaSuccess) return set_cuda_error("dd_forward: launch", e);

@@ -49,52 +49,6 @@ struct FwdArgs {
   int* status;             // device error word
 };
 
-// One beam of a batch (device-resident descriptor) and one work item.
-struct BatchBeam {
-  const void* in;
-  int64_t in_stride;
-  void* out;
-  int64_t out_stride;
-  const int32_t* delaysT;  // the beam's plan table [C][n_dm_pad]
-  int32_t C;
-  int32_t n_dm;
-  int32_t n_dm_pad;
-  int32_t pitch;           // staged row pitch for the batch's tile shape
-  int64_t n_out;
-  int64_t n_in;
-};
-struct BatchItem {
-  int32_t beam;
-  int32_t tile_d;  // DM block
-  int32_t tile_t;  // time block
-  int32_t pad;
-};
-
-__host__ __device__ inline FwdArgs batch_args(const BatchBeam& b, int* status) {
-  FwdArgs a{};
-  a.in = b.in;
-  a.in_stride = b.in_stride;
-  a.w = nullptr;
-  a.out = b.out;
-  a.out_stride = b.out_stride;
-  a.delaysT = b.delaysT;
-  a.C = b.C;
-  a.n_dm = b.n_dm;
-  a.n_dm_pad = b.n_dm_pad;
-  a.n_out = b.n_out;
-  a.n_in = b.n_in;
-  a.status = status;
-  return a;
-}
-
-// Persistent batch launches (fwd_kernels.cu): the f32 batch uses the STAGED
-// tile shape kBatchF32, the uint8 batch the U8PK shape kBatchU8.
-TileConfig batch_config(dd_dtype dtype);
-int batch_smem_for(dd_dtype dtype, int pitch);
-int batch_blocks_per_sm(dd_dtype dtype, int smem);
-cudaError_t launch_batch(dd_dtype dtype, const BatchBeam* beams, const BatchItem* items, int n_items, int* counter,
-                         int* status, int smem, int grid, cudaStream_t s);
-
 // TMW6 needs 16-byte aligned input rows of a multiple of 32 floats (128 bytes).
 bool tmw6_accepts(const void* in, int64_t in_stride);
 

@@ -209,30 +209,6 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
   (void)staged_tile<Tin, WEIGHTED, BD, BT, CC, STAGES>(a, pitch, blockIdx.x, blockIdx.y, kbase, smem_raw);
 }
 
-// Persistent form for batches of beams: each block pulls (beam, DM block,
-// time block) items from an atomic counter until the list is exhausted.
-template <typename Tin, int BD, int BT, int CC, int STAGES>
-__global__ void __launch_bounds__(256) fwd_staged_persistent(const BatchBeam* __restrict__ beams,
-                                                              const BatchItem* __restrict__ items, int n_items,
-                                                              int* counter, int* status) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ int s_item;
-  init_stage_bars(reinterpret_cast<uint64_t*>(smem_raw), STAGES);
-  uint32_t kbase = 0;
-  while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();  // also: the previous tile is finished with shared memory
-    const int it = s_item;
-    __syncthreads();
-    if (it >= n_items) break;
-    const BatchItem item = items[it];
-    const FwdArgs a = batch_args(beams[item.beam], status);
-    if (!staged_tile<Tin, false, BD, BT, CC, STAGES>(a, beams[item.beam].pitch, item.tile_t, item.tile_d, kbase,
-                                                     smem_raw))
-      break;
-  }
-}
-
 // ------------------------------------------------------------------- U8PK
 // uint8 -> int32 with packed 16-bit accumulation.  The block stages byte spans
 // exactly like STAGED.  A warp owns DPW DM trials x 32 lanes x 28 samples (7
@@ -419,27 +395,6 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
   (void)u8pk_tile<WD, WT, DPW, CC, STAGES>(a, pitch, blockIdx.x, blockIdx.y, kbase, smem_raw);
 }
 
-template <int WD, int WT, int DPW, int CC, int STAGES>
-__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_persistent(const BatchBeam* __restrict__ beams,
-                                                                     const BatchItem* __restrict__ items, int n_items,
-                                                                     int* counter, int* status) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  __shared__ int s_item;
-  init_stage_bars(reinterpret_cast<uint64_t*>(smem_raw), STAGES);
-  uint32_t kbase = 0;
-  while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-    __syncthreads();  // also: the previous tile is finished with shared memory
-    const int it = s_item;
-    __syncthreads();
-    if (it >= n_items) break;
-    const BatchItem item = items[it];
-    const FwdArgs a = batch_args(beams[item.beam], status);
-    if (!u8pk_tile<WD, WT, DPW, CC, STAGES>(a, beams[item.beam].pitch, item.tile_t, item.tile_d, kbase, smem_raw))
-      break;
-  }
-}
-
 __host__ __device__ constexpr int u8pk_smem_bytes(int stages, int cc, int bd, int pitch, int nw, int dpw) {
   return (stages * cc * pitch + stages * cc * bd * 4) > nw * dpw * 32 * 28 * 4
              ? kStBarBytes + (stages * cc * pitch + stages * cc * bd * 4)
@@ -569,53 +524,6 @@ int u8pk_smem_for(const TileConfig& cfg, int pitch) {
 int staged_smem_for(dd_dtype dtype, int stages, int cc, int bd, int pitch) {
   return dtype == DD_U8_I32 ? staged_smem_bytes<uint8_t>(stages, cc, bd, pitch)
                             : staged_smem_bytes<float>(stages, cc, bd, pitch);
-}
-
-// ------------------------------------------------------------------ batches
-// Tile shapes of the persistent batch kernels (the measured-fastest STAGED
-// and U8PK shapes on the Apertif setup).
-#define DD_BATCH_F32 8, 1024, 4, 3       /* BD, BT, CC, STAGES */
-#define DD_BATCH_U8 8, 1, 2, 16, 4       /* WD, WT, DPW, CC, STAGES */
-
-TileConfig batch_config(dd_dtype dtype) {
-  if (dtype == DD_U8_I32) return {Kind::U8Pk, 16, 32 * 28, 16, 4, 256, 28, 0, 0, "u8pk_w8x1_d2_c16_st4"};
-  return {Kind::Staged, 8, 1024, 4, 3, 256, 0, 0, 0, "staged_d8_t1024_c4_s3"};
-}
-
-int batch_smem_for(dd_dtype dtype, int pitch) {
-  if (dtype == DD_U8_I32) return u8pk_smem_bytes(4, 16, 16, pitch, 8, 2);
-  return staged_smem_bytes<float>(3, 4, 8, pitch);
-}
-
-int batch_blocks_per_sm(dd_dtype dtype, int smem) {
-  int n = 0;
-  cudaError_t e;
-  if (dtype == DD_U8_I32) {
-    auto k = fwd_u8pk_persistent<DD_BATCH_U8>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, smem);
-  } else {
-    auto k = fwd_staged_persistent<float, DD_BATCH_F32>;
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, 256, smem);
-  }
-  return e == cudaSuccess ? n : 0;
-}
-
-cudaError_t launch_batch(dd_dtype dtype, const BatchBeam* beams, const BatchItem* items, int n_items, int* counter,
-                         int* status, int smem, int grid, cudaStream_t s) {
-  if (dtype == DD_U8_I32) {
-    auto k = fwd_u8pk_persistent<DD_BATCH_U8>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, 256, smem, s>>>(beams, items, n_items, counter, status);
-  } else {
-    auto k = fwd_staged_persistent<float, DD_BATCH_F32>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
-    k<<<grid, 256, smem, s>>>(beams, items, n_items, counter, status);
-  }
-  return cudaGetLastError();
 }
 
 }  // namespace dd

@@ -85,10 +85,12 @@ def beam_bytes(spec: BeamSpec) -> int:
     elem = 1 if spec.dtype == "u8" else 4
     d = binding.delay_table(s.channels, s.f_low_mhz, s.chan_bw_mhz, s.t_samp_s, s.dm_first, s.dm_step, s.n_dm)
     max_d = int(d.max())
-    v = 16 // elem
+    v = 128 // elem                                   # tail buffers use 128-byte rows
     stride = (max_d + spec.chunk_len + v - 1) // v * v
     n_dm_pad = (s.n_dm + 63) // 64 * 64
-    tables = 4 * s.channels * (s.n_dm + n_dm_pad) + 16 * s.channels * (n_dm_pad // 8 + n_dm_pad // 4)
+    tables = 4 * s.channels * (s.n_dm + n_dm_pad)     # delay table and its transposed copy
+    if spec.dtype == "f32":                           # 6-trial window descriptors (at most)
+        tables += 16 * s.channels * ((s.n_dm + 5) // 6)
     return int(2 * s.channels * stride * elem + s.channels * spec.chunk_len * elem +
                4 * s.n_dm * spec.chunk_len + tables)
 
@@ -131,22 +133,25 @@ class Server:
         # per-beam arrival clock starts when the beam is admitted
         arrivals: list[tuple[float, str, int]] = []
 
-        def admit(now):
+        def admit():
             nonlocal in_use, peak_in_use, peak_beams
+            newly = []
             while waiting and in_use + need[waiting[0].name] <= self.budget:
                 sp = waiting.pop(0)
                 with torch.cuda.device(self.device):
-                    act = _Active(sp, torch, self.device)
-                active[sp.name] = act
+                    active[sp.name] = _Active(sp, torch, self.device)
+                newly.append(sp)
                 in_use += need[sp.name]
                 peak_in_use = max(peak_in_use, in_use)
                 peak_beams = max(peak_beams, len(active))
-                now = time.perf_counter()     # the beam's clock starts once its resources exist
+            # the admitted beams' clocks start together, once all their resources exist
+            now = time.perf_counter()
+            for sp in newly:
                 admitted_at[sp.name] = now
                 for k in range(sp.n_chunks):
                     heapq.heappush(arrivals, (now + (sp.phase_s + k * sp.period_s) * time_scale, sp.name, k))
 
-        admit(time.perf_counter())
+        admit()
         ready: list[tuple[float, str, int]] = []
         with torch.cuda.device(self.device):
             while active or waiting:
@@ -187,7 +192,7 @@ class Server:
                             act.close()
                             del active[name]
                             in_use -= need[name]
-                            admit(time.perf_counter())
+                            admit()
                 if not ready and arrivals and all(a.pending is None for a in active.values()):
                     time.sleep(max(0.0, min(poll_s * 10, arrivals[0][0] - time.perf_counter())))
                 else:
