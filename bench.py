@@ -169,6 +169,41 @@ def cpu_baseline(setup, dtype, target_s=12.0, seed=0):
                       f"{setup.channels} channels, {dtype}, single-threaded C oracle, {el:.1f} s"}
 
 
+def cpu_baseline_parallel(setup, dtype, target_s=8.0, seed=0):
+    """The multi-threaded CPU baseline (the paper's CPU comparison): tune threads,
+    DM chunk and time block on a small sample, then time a bounded sample of the
+    workload on all host cores.  float32 only (the uint8 path is timed as float)."""
+    import oracle
+    oracle.build()
+    d = oracle.delay_table(*setup.plan_args()[:7])
+    n_in = setup.n_out + int(d.max())
+    x = synth.noise_f32(seed, setup.channels, n_in)
+    all_threads = oracle.cpu_threads()
+    probe = np.ascontiguousarray(d[np.linspace(0, setup.n_dm - 1, 4 * all_threads).astype(np.int64)])
+    best = None
+    for threads in sorted({all_threads, max(1, all_threads // 2)}):
+        for dm_chunk in (1, 4):
+            for t_block in (1024, 4096):
+                t = time.perf_counter()
+                oracle.forward_f32_parallel(probe, x, setup.n_out, None, threads, dm_chunk, t_block)
+                el = time.perf_counter() - t
+                if best is None or el < best[0]:
+                    best = (el, threads, dm_chunk, t_block)
+    _, threads, dm_chunk, t_block = best
+    per_row = best[0] / len(probe)
+    rows = int(max(1, min(setup.n_dm, target_s / per_row)))
+    idx = np.linspace(0, setup.n_dm - 1, rows).astype(np.int64)
+    sub = np.ascontiguousarray(d[idx])
+    t = time.perf_counter()
+    oracle.forward_f32_parallel(sub, x, setup.n_out, None, threads, dm_chunk, t_block)
+    el = time.perf_counter() - t
+    return {"value": rows * setup.n_out / el, "unit": UNIT, "cores": threads, "kind": "openmp",
+            "tuned": {"threads": threads, "dm_chunk": dm_chunk, "t_block": t_block},
+            "sample": f"{rows} of {setup.n_dm} DM trials (evenly spaced) x {setup.n_out} samples x "
+                      f"{setup.channels} channels, float32 summed in fp64, {el:.1f} s on {threads} threads "
+                      f"of {os.cpu_count()} host cores"}
+
+
 def run_reference(args, setup):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -333,6 +368,7 @@ def run_ours(args, setup):
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(setup, args.dtype)
+        line["cpu_baseline_parallel"] = cpu_baseline_parallel(setup, args.dtype)
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

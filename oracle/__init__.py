@@ -14,6 +14,11 @@ Two independent forms live here:
 * ``brute_*`` functions below: the same definitions as pure-Python loops over
   numpy scalars, for tiny inputs only, as a second opinion on the C code.
 
+Beside the oracle, ``cpu_parallel.c`` is the multi-threaded CPU baseline (the
+paper's CPU comparison, Section 5): the oracle's fp64 sum with DM trials
+spread over the host's cores, used only by ``bench.py``'s CPU-baseline leg
+and checked bit for bit against the oracle in the tests.
+
 Each function cites the passage of the paper it follows.
 """
 from __future__ import annotations
@@ -29,8 +34,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dd_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _SO = os.path.join(_BUILD, "liboracle.so")
+_PAR_SRC = os.path.join(_HERE, "cpu_parallel.c")
+_PAR_SO = os.path.join(_BUILD, "libcpuparallel.so")
 _lock = threading.Lock()
 _lib = None
+_par = None
 
 
 def build(force: bool = False) -> str:
@@ -41,6 +49,14 @@ def build(force: bool = False) -> str:
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", _SRC,
                                "-o", tmp, "-lm"])
         os.replace(tmp, _SO)
+    if force or not os.path.exists(_PAR_SO) or os.path.getmtime(_PAR_SO) < os.path.getmtime(_PAR_SRC):
+        tmp = _PAR_SO + f".tmp{os.getpid()}"
+        base = ["gcc", "-O3", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", _PAR_SRC, "-o", tmp]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:   # no OpenMP: the same code, one thread
+            subprocess.check_call(base)
+        os.replace(tmp, _PAR_SO)
     return _SO
 
 
@@ -76,6 +92,21 @@ class OracleError(RuntimeError):
 def _check(rc: int, what: str):
     if rc != 0:
         raise OracleError(f"{what} failed with oracle code {rc}")
+
+
+def _load_parallel():
+    global _par
+    with _lock:
+        if _par is None:
+            build()
+            lib = ctypes.CDLL(_PAR_SO)
+            i32, i64, vp = ctypes.c_int32, ctypes.c_int64, ctypes.c_void_p
+            lib.cpb_max_threads.argtypes = []
+            lib.cpb_max_threads.restype = ctypes.c_int
+            lib.cpb_forward_f32.argtypes = [i32, i32, i64, i64, vp, vp, vp, vp, i32, i32, i32]
+            lib.cpb_forward_f32.restype = ctypes.c_int
+            _par = lib
+    return _par
 
 
 # ---------------------------------------------------------------- C-backed API
@@ -183,4 +214,28 @@ def brute_forward(d, x, n_out, w=None):
                 v = x[c, s + d[dm, c]]
                 acc += (float(w[c]) * float(v)) if w is not None else (int(v) if x.dtype == np.uint8 else float(v))
             out[dm, s] = acc
+    return out
+
+
+# ------------------------------------------------- multi-threaded CPU baseline
+
+def cpu_threads() -> int:
+    """Threads the multi-threaded baseline uses by default (1 without OpenMP)."""
+    return int(_load_parallel().cpb_max_threads())
+
+
+def forward_f32_parallel(d: np.ndarray, x: np.ndarray, n_out: int, w: np.ndarray | None = None,
+                         threads: int = 0, dm_chunk: int = 4, t_block: int = 2048) -> np.ndarray:
+    """Algorithm 1 on the host's cores: the oracle's fp64 sums, bit for bit.
+
+    threads = 0 uses every core; DM trials go to threads in chunks of
+    ``dm_chunk``; time runs in blocks of ``t_block`` samples."""
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    if w is not None:
+        w = np.ascontiguousarray(w, dtype=np.float32)
+    n_dm, C = d.shape
+    out = np.empty((n_dm, n_out), dtype=np.float64)
+    _check(_load_parallel().cpb_forward_f32(C, n_dm, n_out, x.shape[1], _ptr(d), _ptr(x), _ptr(w), _ptr(out),
+                                            threads, dm_chunk, t_block), "forward_f32_parallel")
     return out

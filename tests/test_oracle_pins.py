@@ -366,3 +366,21 @@ def test_loss_invariances_and_gradient():
         m[i, t] -= h
         fd = (orc.boxcar_snr_loss(p, False)[0] - orc.boxcar_snr_loss(m, False)[0]) / (2 * h)
         assert abs(fd - grad[i, t]) < 1e-6, (i, t, fd, grad[i, t])
+
+
+def test_parallel_cpu_baseline_matches_oracle_bit_for_bit():
+    """The multi-threaded CPU baseline sums the same fp64 terms in the same
+    channel order as the oracle, for any thread count and block sizes."""
+    import oracle
+    from paper_1601_01165_gb300 import synth
+    s = synth.Setup("cpb", 48, 1420.0, 6.25, 50e-6, 0.0, 0.5, 23, 3001)
+    d = oracle.delay_table(*s.plan_args()[:7])
+    x = synth.noise_f32(4, s.channels, s.n_out + int(d.max()) + 5)
+    w = synth.weights(4, s.channels)
+    ref = oracle.forward_f32(d, x, s.n_out, w)
+    for threads, dm_chunk, t_block in [(0, 1, 64), (1, 4, 2048), (3, 5, 1000), (0, 23, 3001)]:
+        got = oracle.forward_f32_parallel(d, x, s.n_out, w, threads, dm_chunk, t_block)
+        assert (got == ref).all(), (threads, dm_chunk, t_block)
+    assert (oracle.forward_f32_parallel(d, x, s.n_out) == oracle.forward_f32(d, x, s.n_out)).all()
+    with pytest.raises(oracle.OracleError):
+        oracle.forward_f32_parallel(d, x[:, :s.n_out], s.n_out)     # input too short for the delays
