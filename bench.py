@@ -436,6 +436,47 @@ def run_batched(args):
     return 0 if same else 1
 
 
+def run_dm_sweep(args):
+    """Auto-tuning across the number of DM trials (Section 4.3, Figs. 3-4): for
+    2, 4, ..., 4096 trials on the Apertif grid, and for perfect data reuse
+    (dm_step = 0, every delay zero, Section 4.2), time every configuration of
+    the plan, keep the fastest, and compare it with the generic one-trial-per-
+    thread kernel (Section 5's "generic" code).  Prints the table and the
+    histogram of tuned configurations."""
+    import tempfile
+    import torch
+    from paper_1601_01165_gb300 import binding as dd
+    torch.cuda.set_device(0)
+    rows, hist = [], {}
+    cases = [(n, synth.APERTIF.dm_step) for n in [2 ** k for k in range(1, 13)]] + [(2048, 0.0)]
+    with tempfile.TemporaryDirectory() as tmp:
+        for dtype in ("f32", "u8"):
+            for n_dm, step in cases:
+                s = synth.APERTIF.replace(n_dm=n_dm, dm_step=step)
+                plan = dd.Plan.from_setup(s, dtype)
+                db = os.path.join(tmp, f"{dtype}_{n_dm}_{step}.jsonl")
+                name, ms = plan.tune(budget_s=0.0, db_path=db)
+                with open(db) as f:
+                    timings = json.loads(f.readline())["timings"]
+                generic = min(v for k, v in timings.items() if k.startswith("naive"))
+                fam = name.split("_")[0]
+                hist[f"{dtype}:{fam}"] = hist.get(f"{dtype}:{fam}", 0) + 1
+                rows.append({"dtype": dtype, "n_dm": n_dm, "dm_step": step, "tuned": name, "tuned_ms": ms,
+                             "generic_ms": generic, "speedup_vs_generic": generic / ms,
+                             "dm_samples_per_s": n_dm * s.n_out / (ms / 1e3), "configs_timed": len(timings)})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                plan.close()
+    units = sum(r["n_dm"] * synth.APERTIF.n_out for r in rows)
+    total_ms = sum(r["tuned_ms"] for r in rows)
+    line = {"metric": METRIC, "workload": "dm-sweep", "value": units / (total_ms / 1e3), "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True, "rows": rows, "histogram": hist,
+            "config": {"workload": "Apertif grid (1024 ch, 20000 samples), 2..4096 DM trials step 0.25, "
+                                   "plus 2048 trials at dm_step 0; float32 and uint8; every configuration timed "
+                                   "(median of 5 after 2 warm-ups, warm L2)"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_serving(args):
     """Real-time serving: Apertif-like uint8 beams delivering 1 s chunks on independent timers."""
     import torch
@@ -483,7 +524,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--dtype", choices=["f32", "u8"], default="f32")
     ap.add_argument("--config", default=None, help="kernel configuration name (default: plan's choice)")
-    ap.add_argument("--workload", choices=["apertif", "lofar", "batched", "serving"], default="apertif")
+    ap.add_argument("--workload", choices=["apertif", "lofar", "batched", "serving", "dm-sweep"], default="apertif")
     ap.add_argument("--beams", type=int, default=None, help="batched: 64, serving: 40")
     ap.add_argument("--chunks", type=int, default=4, help="serving: chunks per beam")
     ap.add_argument("--budget-gb", type=float, default=None, help="serving: HBM budget")
@@ -499,6 +540,8 @@ def main():
     if args.workload == "serving":
         args.beams = args.beams or 40
         return run_serving(args)
+    if args.workload == "dm-sweep":
+        return run_dm_sweep(args)
     setup = synth.APERTIF if args.workload == "apertif" else synth.LOFAR
     if args.impl == "reference":
         return run_reference(args, setup)
