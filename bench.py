@@ -529,6 +529,8 @@ def main():
     ap.add_argument("--chunks", type=int, default=4, help="serving: chunks per beam")
     ap.add_argument("--budget-gb", type=float, default=None, help="serving: HBM budget")
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--n-out", type=int, default=None,
+                    help="output samples per beam instead of the setup's (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -543,6 +545,8 @@ def main():
     if args.workload == "dm-sweep":
         return run_dm_sweep(args)
     setup = synth.APERTIF if args.workload == "apertif" else synth.LOFAR
+    if args.n_out:
+        setup = setup.replace(n_out=args.n_out)
     if args.impl == "reference":
         return run_reference(args, setup)
     return run_ours(args, setup)
