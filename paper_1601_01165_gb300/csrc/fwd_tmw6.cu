@@ -15,7 +15,8 @@
 //    2p + 1.  Each channel it issues two 32-column loads at column shift + o_j
 //    (o_j = delay(c, i0 + j) - delay(c, i0)) and waits once; 64 adds follow.
 //  * Warp p of a quadrant writes the quadrant's windows of channels c = p
-//    (mod 3), three channels ahead, while its own TMEM loads are in flight.
+//    (mod 3) of the next step of three channels, while its TMEM loads of the
+//    step's last channel are in flight.
 //    The input comes from its private stages: a 3-D TMA load (128-byte
 //    swizzle) of the quadrant's 35 rows of 32 samples from the row holding
 //    t0 + delay(c, i0), plus the channel's 16-byte descriptor (base delay,
@@ -239,8 +240,8 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
       float v0[32], v1[32];
       tmem_ld32(col + (bytes & 0xffu), v0);
       tmem_ld32(col + ((bytes >> 8) & 0xffu), v1);
-      // while the first loads are in flight: this warp's window of the next step
-      if (k == 0 && ok) {
+      // while the step's last loads are in flight: this warp's window of the next step
+      if (k == kLead - 1 && ok) {
         const int cn = kLead * (n + 1) + p;
         if (cn < C) ok = write_window(cn, (kLead - set) + p);
       }
