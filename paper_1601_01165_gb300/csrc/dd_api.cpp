@@ -1,6 +1,8 @@
 // C ABI: errors, forward on device buffers and on host buffers.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -30,19 +32,14 @@ dd_status set_cuda_error(const char* where, cudaError_t e) {
 
 void clear_error() { g_last_error.clear(); }
 
-// Validated launch of the selected (or a fallback) forward kernel.
-dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
-                         int64_t out_stride, cudaStream_t stream, int cfg_override) {
-  if (!in || !out) return set_error(DD_ERR_ARG, "dd_forward: in/out is NULL");
-  if (in_stride < p->n_in)
-    return set_error(DD_ERR_SHAPE, "dd_forward: in_row_stride %lld < n_in %lld", (long long)in_stride,
-                     (long long)p->n_in);
-  if (out_stride < p->n_out)
-    return set_error(DD_ERR_SHAPE, "dd_forward: out_row_stride %lld < n_out %lld", (long long)out_stride,
-                     (long long)p->n_out);
-  if (p->dtype == DD_U8_I32 && w)
-    return set_error(DD_ERR_UNSUPPORTED, "dd_forward: uint8 plans take unit weights only (w must be NULL)");
+// Launch of the selected (or a fallback) forward kernel over output samples
+// [t0, t1) (arguments already validated; t0 a multiple of 128 samples keeps
+// every alignment the kernels rely on).
+static dd_status launch_range(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
+                              int64_t out_stride, int64_t t0, int64_t t1, cudaStream_t stream, int cfg_override) {
   const int elem = p->dtype == DD_U8_I32 ? 1 : 4;
+  in = static_cast<const unsigned char*>(in) + t0 * elem;
+  out = static_cast<unsigned char*>(out) + t0 * 4;
   FwdArgs a{};
   a.in = in;
   a.in_stride = in_stride;
@@ -55,8 +52,8 @@ dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const 
   a.C = p->C;
   a.n_dm = p->n_dm;
   a.n_dm_pad = p->n_dm_pad;
-  a.n_out = p->n_out;
-  a.n_in = p->n_in;
+  a.n_out = t1 - t0;
+  a.n_in = (t1 - t0) + p->max_delay;
   a.status = p->d_status;
   int k = cfg_override >= 0 ? cfg_override : p->selected;
   const TileConfig* cfg = &p->configs[k];
@@ -74,6 +71,21 @@ dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const 
   cudaError_t e = launch_forward(*cfg, p->dtype, a, stream);
   if (e != cudaSuccess) return set_cuda_error("dd_forward: launch", e);
   return DD_OK;
+}
+
+// Validated launch of the selected (or a fallback) forward kernel.
+dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
+                         int64_t out_stride, cudaStream_t stream, int cfg_override) {
+  if (!in || !out) return set_error(DD_ERR_ARG, "dd_forward: in/out is NULL");
+  if (in_stride < p->n_in)
+    return set_error(DD_ERR_SHAPE, "dd_forward: in_row_stride %lld < n_in %lld", (long long)in_stride,
+                     (long long)p->n_in);
+  if (out_stride < p->n_out)
+    return set_error(DD_ERR_SHAPE, "dd_forward: out_row_stride %lld < n_out %lld", (long long)out_stride,
+                     (long long)p->n_out);
+  if (p->dtype == DD_U8_I32 && w)
+    return set_error(DD_ERR_UNSUPPORTED, "dd_forward: uint8 plans take unit weights only (w must be NULL)");
+  return launch_range(p, in, in_stride, w, out, out_stride, 0, p->n_out, stream, cfg_override);
 }
 
 }  // namespace dd
@@ -140,18 +152,69 @@ extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_
     if (cudaMalloc(&plan->h_dev_w, (size_t)plan->C * sizeof(float)) != cudaSuccess)
       return set_error(DD_ERR_NOMEM, "dd_forward_host: cannot allocate weights");
   }
-  cudaError_t e = cudaMemcpy2DAsync(plan->h_dev_in, dev_in_stride * elem, host_in, in_row_stride * elem,
-                                    plan->n_in * elem, plan->C, cudaMemcpyHostToDevice, s);
+  // The output runs in up to three time chunks as a pipeline on three
+  // plan-owned streams: the copy-in of the input columns chunk k needs beyond
+  // those already on the device, chunk k's kernel, and chunk k's copy-out.
+  // A short first chunk lets the kernels start early, a short last chunk lets
+  // the copy-out finish soon after them, and the middle chunk keeps the
+  // kernel's grid large; the copies of the other chunks overlap the kernels.
+  // Each output element is computed as in one launch: the result is
+  // bit-identical.  Chunk edges are multiples of 4096 samples.
+  constexpr int64_t kEdge = 4096;
+  int64_t edges[4] = {0, plan->n_out, plan->n_out, plan->n_out};
+  int n_chunks = 1;
+  if (plan->n_out > 3 * kEdge) {
+    const int64_t last = plan->n_out - (plan->n_out - 1) / kEdge * kEdge;  // 1..4096
+    edges[1] = kEdge;
+    edges[2] = plan->n_out - last;
+    edges[3] = plan->n_out;
+    n_chunks = 3;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!plan->h_streams[0]) {
+    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+      e = cudaStreamCreateWithFlags(&plan->h_streams[k], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return set_cuda_error("dd_forward_host: streams", e);
+  }
+  while ((int)plan->h_events.size() < 2 * n_chunks + 2) {
+    cudaEvent_t ev = nullptr;
+    e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return set_cuda_error("dd_forward_host: events", e);
+    plan->h_events.push_back(ev);
+  }
+  cudaStream_t s_in = plan->h_streams[0], s_run = plan->h_streams[1], s_out = plan->h_streams[2];
+  cudaEvent_t ev_fork = plan->h_events[0], ev_done = plan->h_events[1];
+  e = cudaEventRecord(ev_fork, s);  // after the caller's earlier work on `stream`
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev_fork, 0);
   if (e == cudaSuccess && host_w)
-    e = cudaMemcpyAsync(plan->h_dev_w, host_w, plan->C * sizeof(float), cudaMemcpyHostToDevice, s);
+    e = cudaMemcpyAsync(plan->h_dev_w, host_w, plan->C * sizeof(float), cudaMemcpyHostToDevice, s_in);
   if (e != cudaSuccess) return set_cuda_error("dd_forward_host: copy in", e);
-  dd_status st = forward_device(plan, plan->h_dev_in, dev_in_stride, host_w ? plan->h_dev_w : nullptr,
-                                plan->h_dev_out, plan->n_out, s, -1);
-  if (st != DD_OK) return st;
-  e = cudaMemcpy2DAsync(host_out, out_row_stride * 4, plan->h_dev_out, plan->n_out * 4, plan->n_out * 4,
-                        plan->n_dm, cudaMemcpyDeviceToHost, s);
-  if (e != cudaSuccess) return set_cuda_error("dd_forward_host: copy out", e);
-  e = cudaStreamSynchronize(s);
+  int64_t have = 0;  // input columns already copied
+  for (int k = 0; k < n_chunks; ++k) {
+    const int64_t t0 = edges[k], t1 = edges[k + 1];
+    const int64_t need = t1 + plan->max_delay;
+    cudaEvent_t ev_in = plan->h_events[2 + 2 * k], ev_run = plan->h_events[3 + 2 * k];
+    e = cudaMemcpy2DAsync(static_cast<unsigned char*>(plan->h_dev_in) + have * elem, dev_in_stride * elem,
+                          static_cast<const unsigned char*>(host_in) + have * elem, in_row_stride * elem,
+                          (need - have) * elem, plan->C, cudaMemcpyHostToDevice, s_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in, s_in);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_run, ev_in, 0);
+    if (e != cudaSuccess) return set_cuda_error("dd_forward_host: copy in", e);
+    have = need;
+    const dd_status st = launch_range(plan, plan->h_dev_in, dev_in_stride, host_w ? plan->h_dev_w : nullptr,
+                                      plan->h_dev_out, plan->n_out, t0, t1, s_run, -1);
+    if (st != DD_OK) return st;
+    e = cudaEventRecord(ev_run, s_run);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_run, 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(static_cast<unsigned char*>(host_out) + t0 * 4, out_row_stride * 4,
+                            static_cast<unsigned char*>(plan->h_dev_out) + t0 * 4, plan->n_out * 4, (t1 - t0) * 4,
+                            plan->n_dm, cudaMemcpyDeviceToHost, s_out);
+    if (e != cudaSuccess) return set_cuda_error("dd_forward_host: copy out", e);
+  }
+  e = cudaEventRecord(ev_done, s_out);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_done, 0);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return set_cuda_error("dd_forward_host: synchronize", e);
   return DD_OK;
 }

@@ -132,19 +132,25 @@ def test_unaligned_input_uses_plain_kernel(dd):
     assert_parity(out.cpu().numpy(), ref, scale, "f32", where="unaligned")
 
 
-def test_forward_host_matches_device(dd):
-    s = synth.Setup("host", 256, 1420.0, 1.171875, 50e-6, 0.0, 0.25, 64, 4000)
+@pytest.mark.parametrize("n_out", [4000, 13000])
+def test_forward_host_matches_device(dd, n_out):
+    """The host-buffer entry point pipelines time chunks (copy in, kernel, copy
+    out on separate streams); 13000 samples make chunks of 4096, 8192 and 712."""
+    s = synth.Setup("host", 256, 1420.0, 1.171875, 50e-6, 0.0, 0.25, 64, n_out)
     for dtype in ("f32", "u8"):
         plan = dd.Plan.from_setup(s, dtype)
         d = oracle_table(s)
         x, _ = make_input(s, dtype, 7, plan.n_in)
+        w = synth.weights(7, s.channels) if dtype == "f32" else None
         xh = torch.from_numpy(x).pin_memory()
-        got = plan.forward_host(xh).numpy()
+        wh = torch.from_numpy(w) if w is not None else None
+        got = plan.forward_host(xh, wh).numpy()
         dev = plan.forward(torch.from_numpy(np.ascontiguousarray(
-            np.pad(x, ((0, 0), (0, plan.padded_in_stride() - plan.n_in))))).cuda()).cpu().numpy()
+            np.pad(x, ((0, 0), (0, plan.padded_in_stride() - plan.n_in))))).cuda(),
+            torch.from_numpy(w).cuda() if w is not None else None).cpu().numpy()
         assert (got == dev).all()
-        ref, scale = oracle_window(d, x, dtype, 0, s.n_dm, 0, s.n_out)
-        assert_parity(got, ref, scale, dtype, where=f"host {dtype}")
+        ref, scale = oracle_window(d, x, dtype, 0, s.n_dm, 0, s.n_out, w)
+        assert_parity(got, ref, scale, dtype, where=f"host {dtype} {n_out}")
 
 
 def test_errors(dd):
