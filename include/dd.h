@@ -129,6 +129,16 @@ dd_status dd_plan_selected_config(dd_plan_t plan, int32_t* k);
  */
 dd_status dd_plan_device_status(dd_plan_t plan, int32_t* code);
 
+/*
+ * Self-check of that path (not in the paper): launches on `stream` a one-warp
+ * kernel that waits, with a limit of `limit_cycles` SM clock cycles (1 ..
+ * 2e9), on an mbarrier phase nothing completes.  The wait expires, the
+ * kernel records code 1 in the plan's status word and returns, and the
+ * context stays usable; dd_plan_device_status then reports it.  Errors:
+ * DD_ERR_ARG (NULL plan, limit out of range), DD_ERR_CUDA (launch failure).
+ */
+dd_status dd_check_wait_timeout(dd_plan_t plan, int64_t limit_cycles, void* stream);
+
 /* ---------------------------------------------------------------- forward */
 
 /*

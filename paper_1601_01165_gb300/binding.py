@@ -69,6 +69,7 @@ def _declare(lib):
         "dd_plan_select_config": (st, [vp, i32]),
         "dd_plan_selected_config": (st, [vp, P32]),
         "dd_plan_device_status": (st, [vp, P32]),
+        "dd_check_wait_timeout": (st, [vp, i64, vp]),
         "dd_forward": (st, [vp, vp, i64, vp, vp, i64, vp]),
         "dd_forward_host": (st, [vp, vp, i64, vp, vp, i64, vp]),
         "dd_adjoint": (st, [vp, vp, i64, vp, vp, i64, vp, i64, vp, vp]),
@@ -210,6 +211,11 @@ class Plan:
         if st not in (0, 8):
             check(st, "dd_plan_device_status")
         return code.value
+
+    def check_wait_timeout(self, limit_cycles=2_000_000, stream=None):
+        """dd_check_wait_timeout: make a bounded wait expire on the GPU (read the result with device_status)."""
+        check(load().dd_check_wait_timeout(self._h, int(limit_cycles), _stream_handle(stream)),
+              "dd_check_wait_timeout")
 
     def alloc_input(self, row_stride=None):
         import torch
