@@ -130,6 +130,34 @@ class ClockSampler:
                 "power_w_max": max((float(r[2]) for r in self.rows if _isnum(r[2])), default=None)}
 
 
+def _pct(xs, q):
+    ys = sorted(xs)
+    return ys[min(len(ys) - 1, int(round(q / 100 * (len(ys) - 1))))]
+
+
+def _host_cpu():
+    """Host CPU model and core count (the CPU baselines run there)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                low = line.lower()
+                if low.startswith("model name") or low.startswith("cpu part") or low.startswith("hardware"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"model": model, "cores": os.cpu_count()}
+
+
 def _isnum(s):
     try:
         float(s)
@@ -300,6 +328,19 @@ def run_ours(args, setup):
         torch.distributed.barrier()
     sampler.stop()
     launch_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
+    # warm L2: the same input buffer every launch (reported beside the cold-L2 headline)
+    warm_ms = None
+    if rank == 0 or ws == 1:
+        kw = max(5, min(args.steps, 20))
+        for _ in range(3):
+            plan.forward(xs[0], out=out)
+        w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        w0.record(stream)
+        for _ in range(kw):
+            plan.forward(xs[0], out=out)
+        w1.record(stream)
+        torch.cuda.synchronize()
+        warm_ms = w0.elapsed_time(w1) / kw
     total_ms = ev[0].elapsed_time(ev[args.steps])
     if ws > 1:
         t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
@@ -364,11 +405,13 @@ def run_ours(args, setup):
                           f"{n_buf} rotating input buffers ({n_buf * in_bytes / 2**20:.0f} MiB > 2x L2)"),
         "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
         "kernel_source_hash": kh,
-        "launch_ms": {"min": min(launch_ms), "median": statistics.median(launch_ms), "max": max(launch_ms)},
+        "launch_ms": {"min": min(launch_ms), "p10": _pct(launch_ms, 10), "median": statistics.median(launch_ms),
+                      "p90": _pct(launch_ms, 90), "max": max(launch_ms), "warm_l2_mean": warm_ms},
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(setup, args.dtype)
         line["cpu_baseline_parallel"] = cpu_baseline_parallel(setup, args.dtype)
+        line["cpu_baseline"]["host"] = line["cpu_baseline_parallel"]["host"] = _host_cpu()
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
