@@ -164,10 +164,11 @@ dd_status dd_forward(dd_plan_t plan, const void* in, int64_t in_row_stride, cons
  * buffers the plan owns, runs the forward kernel and copies the result back
  * to `host_out`, then waits for `stream`.  Outputs longer than 12288 samples
  * run in three time chunks (4096 samples, the middle, the last partial 4096)
- * as a pipeline on three streams the plan owns (copy of the input columns
- * chunk k adds, chunk k's kernel, copy-out of chunk k), forked from and joined
- * back into `stream`, so the copies overlap the kernels; the result is
- * bit-identical to one dd_forward.  Layouts as for dd_forward.
+ * as a pipeline on streams the plan owns (one for the copies of the input
+ * columns chunk k adds, two each for the kernels and the copies out,
+ * alternating between chunks), forked from and joined back into `stream`, so
+ * the copies overlap the kernels; the result is bit-identical to one
+ * dd_forward.  Layouts as for dd_forward.
  * Page-locked host memory gives full copy bandwidth (and is needed for the
  * copies to overlap).  The plan's staging buffers, streams and events are
  * created on first use and kept until the plan is destroyed (DD_ERR_NOMEM if

@@ -152,9 +152,9 @@ extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_
     if (cudaMalloc(&plan->h_dev_w, (size_t)plan->C * sizeof(float)) != cudaSuccess)
       return set_error(DD_ERR_NOMEM, "dd_forward_host: cannot allocate weights");
   }
-  // The output runs in up to three time chunks as a pipeline on three
-  // plan-owned streams: the copy-in of the input columns chunk k needs beyond
-  // those already on the device, chunk k's kernel, and chunk k's copy-out.
+  // The output runs in up to three time chunks as a pipeline on plan-owned
+  // streams: the copy-in of the input columns chunk k needs beyond those
+  // already on the device, chunk k's kernel, and chunk k's copy-out.
   // A short first chunk lets the kernels start early, a short last chunk lets
   // the copy-out finish soon after them, and the middle chunk keeps the
   // kernel's grid large; the copies of the other chunks overlap the kernels.
@@ -172,7 +172,7 @@ extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_
   }
   cudaError_t e = cudaSuccess;
   if (!plan->h_streams[0]) {
-    for (int k = 0; k < 3 && e == cudaSuccess; ++k)
+    for (int k = 0; k < 5 && e == cudaSuccess; ++k)
       e = cudaStreamCreateWithFlags(&plan->h_streams[k], cudaStreamNonBlocking);
     if (e != cudaSuccess) return set_cuda_error("dd_forward_host: streams", e);
   }
@@ -182,8 +182,11 @@ extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_
     if (e != cudaSuccess) return set_cuda_error("dd_forward_host: events", e);
     plan->h_events.push_back(ev);
   }
-  cudaStream_t s_in = plan->h_streams[0], s_run = plan->h_streams[1], s_out = plan->h_streams[2];
-  cudaEvent_t ev_fork = plan->h_events[0], ev_done = plan->h_events[1];
+  // chunks alternate between two kernel streams (and two copy-out streams),
+  // so a short chunk's blocks fill the last wave of its neighbour's
+  cudaStream_t s_in = plan->h_streams[0];
+  cudaStream_t s_run[2] = {plan->h_streams[1], plan->h_streams[2]}, s_out[2] = {plan->h_streams[3], plan->h_streams[4]};
+  cudaEvent_t ev_fork = plan->h_events[0];
   e = cudaEventRecord(ev_fork, s);  // after the caller's earlier work on `stream`
   if (e == cudaSuccess) e = cudaStreamWaitEvent(s_in, ev_fork, 0);
   if (e == cudaSuccess && host_w)
@@ -198,22 +201,24 @@ extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_
                           static_cast<const unsigned char*>(host_in) + have * elem, in_row_stride * elem,
                           (need - have) * elem, plan->C, cudaMemcpyHostToDevice, s_in);
     if (e == cudaSuccess) e = cudaEventRecord(ev_in, s_in);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_run, ev_in, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_run[k & 1], ev_in, 0);
     if (e != cudaSuccess) return set_cuda_error("dd_forward_host: copy in", e);
     have = need;
     const dd_status st = launch_range(plan, plan->h_dev_in, dev_in_stride, host_w ? plan->h_dev_w : nullptr,
-                                      plan->h_dev_out, plan->n_out, t0, t1, s_run, -1);
+                                      plan->h_dev_out, plan->n_out, t0, t1, s_run[k & 1], -1);
     if (st != DD_OK) return st;
-    e = cudaEventRecord(ev_run, s_run);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out, ev_run, 0);
+    e = cudaEventRecord(ev_run, s_run[k & 1]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s_out[k & 1], ev_run, 0);
     if (e == cudaSuccess)
       e = cudaMemcpy2DAsync(static_cast<unsigned char*>(host_out) + t0 * 4, out_row_stride * 4,
                             static_cast<unsigned char*>(plan->h_dev_out) + t0 * 4, plan->n_out * 4, (t1 - t0) * 4,
-                            plan->n_dm, cudaMemcpyDeviceToHost, s_out);
+                            plan->n_dm, cudaMemcpyDeviceToHost, s_out[k & 1]);
     if (e != cudaSuccess) return set_cuda_error("dd_forward_host: copy out", e);
   }
-  e = cudaEventRecord(ev_done, s_out);
-  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev_done, 0);
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {  // join both copy-out streams
+    e = cudaEventRecord(plan->h_events[1 - k], s_out[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->h_events[1 - k], 0);
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return set_cuda_error("dd_forward_host: synchronize", e);
   return DD_OK;

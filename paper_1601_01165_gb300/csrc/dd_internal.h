@@ -93,7 +93,7 @@ struct dd_plan_s {
   void* h_dev_out = nullptr;
   float* h_dev_w = nullptr;
   size_t h_in_bytes = 0, h_out_bytes = 0;
-  cudaStream_t h_streams[3] = {};     // copy-in, kernels, copy-out of the host-buffer pipeline
+  cudaStream_t h_streams[5] = {};     // host-buffer pipeline: copy-in, 2 kernel, 2 copy-out streams
   std::vector<cudaEvent_t> h_events;  // fork, done, then (copied-in, computed) per chunk
   // adjoint: the transposed plan (channels and DM trials swapped, delays
   // max_delay - delay) and its zero-padded copy of grad_out

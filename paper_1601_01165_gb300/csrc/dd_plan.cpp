@@ -97,7 +97,7 @@ void free_plan_device(dd_plan_s* p) {
   cudaFree(p->h_dev_in);
   cudaFree(p->h_dev_out);
   cudaFree(p->h_dev_w);
-  for (int k = 0; k < 3; ++k)
+  for (int k = 0; k < 5; ++k)
     if (p->h_streams[k]) cudaStreamDestroy(p->h_streams[k]);
   for (cudaEvent_t ev : p->h_events) cudaEventDestroy(ev);
   p->h_events.clear();
@@ -113,7 +113,7 @@ void free_plan_device(dd_plan_s* p) {
   p->d_status = nullptr;
   p->h_dev_in = p->h_dev_out = nullptr;
   p->h_dev_w = nullptr;
-  for (int k = 0; k < 3; ++k) p->h_streams[k] = nullptr;
+  for (int k = 0; k < 5; ++k) p->h_streams[k] = nullptr;
   p->adj_pad = p->adj_g = nullptr;
 }
 
