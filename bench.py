@@ -63,12 +63,17 @@ def _peaks():
 
 
 def _kernel_hash():
-    """Hash of the sources the forward kernels are built from (traffic figures are tied to it)."""
+    """Hash of the code the forward kernels are built from, comments and blank
+    space removed (the traffic figures are tied to it)."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_01165_gb300", "csrc")
     for name in ("fwd_kernels.cu", "fwd_tmw6.cu", "ptx.cuh", "dd_internal.h"):
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(csrc, name)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

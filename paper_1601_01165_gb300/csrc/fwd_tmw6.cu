@@ -4,31 +4,34 @@
 // Section 2 notes that nearby DM trials read nearly the same input samples;
 // Section 2.2 exploits it by sharing staged input within a work group.  Here
 // the sharing happens in Tensor Memory, which a warp can read at a run-time
-// column address (registers cannot be indexed at run time) and at ~3.5x the
-// shared-memory bandwidth:
+// column address (registers cannot be indexed at run time) and which returns
+// values to registers several times faster than shared memory:
 //
 //  * TMEM lane r holds, per channel, the window of the input that lane r's 32
-//    output samples need for all 6 trials: 32 + max offset columns, aligned
-//    down to 4 floats.  Windows live in a ring of 7 slots of 68 columns.
+//    output samples need for all 6 trials: 32 + max offset columns, taken as
+//    whole 16-float groups of the tile.  Two sets of three 80-column slots
+//    hold the current step's windows and the next step's.
 //  * 12 warps, 3 per TMEM lane quadrant (warp w serves lanes 32 (w % 4) ..,
 //    which is also its SM sub-partition); warp p = w / 4 owns trials 2p and
 //    2p + 1.  Each channel it issues two 32-column loads at column shift + o_j
 //    (o_j = delay(c, i0 + j) - delay(c, i0)) and waits once; 64 adds follow.
-//  * Warp p of a quadrant writes the quadrant's windows of channels c = p
-//    (mod 3) of the next step of three channels, while its TMEM loads of the
-//    step's last channel are in flight.
-//    The input comes from its private stages: a 3-D TMA load (128-byte
-//    swizzle) of the quadrant's 35 rows of 32 samples from the row holding
-//    t0 + delay(c, i0), plus the channel's 16-byte descriptor (base delay,
-//    column bytes, window width); 16-byte shared loads read the swizzled rows
-//    without bank conflicts.  Once a window is out, the warp reloads the
-//    stage with its channel nine later, so quadrants never wait on each other.
+//  * Warp p of a quadrant writes the quadrant's window of channel p of the
+//    next step of three channels, while its TMEM loads of the step's last
+//    channel are in flight.  The input comes from its private stages: a 3-D
+//    TMA load (128-byte swizzle) of the quadrant's 35 rows of 32 samples from
+//    the row holding t0 + delay(c, i0), plus the channel's 16-byte descriptor
+//    (base delay, column bytes, window width); 16-byte shared loads read the
+//    swizzled rows without bank conflicts.  Once a window is out, the warp
+//    reloads the stage with its channel nine later, so quadrants never wait
+//    on each other.
+//  * The quadrant's three warps meet at a named barrier after each step: the
+//    next step's windows are then in TMEM and this step's slots are free.
 //
-// mbarriers: stage full (TMA bytes), window full (the writer), window empty
-// (the quadrant's three readers).  Every wait is bounded; a timeout sets the
-// status word and ends the block.  Sums run in channel order as in every
-// kernel here, so results are bit-identical to theirs.  The 6 x 4096 sums
-// leave through a swizzled shared-memory tile with coalesced 16-byte stores.
+// Stage-full mbarriers count the TMA bytes; every wait on them is bounded and
+// a timeout sets the status word (the warps still run every step, so every
+// named barrier completes).  Sums run in channel order as in every kernel
+// here, so results are bit-identical to theirs.  The 6 x 4096 sums leave
+// through a swizzled shared-memory tile with coalesced 16-byte stores.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
