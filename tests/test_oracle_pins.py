@@ -384,3 +384,33 @@ def test_parallel_cpu_baseline_matches_oracle_bit_for_bit():
     assert (oracle.forward_f32_parallel(d, x, s.n_out) == oracle.forward_f32(d, x, s.n_out)).all()
     with pytest.raises(oracle.OracleError):
         oracle.forward_f32_parallel(d, x[:, :s.n_out], s.n_out)     # input too short for the delays
+
+
+def test_oracle_adjoint_and_weight_gradient_pass_gradcheck():
+    """torch.autograd.gradcheck on the oracle path (CPU, fp64 outputs): the
+    oracle's transpose and weight gradient are the derivatives of its forward
+    sum (the sum is bilinear in (input, weights), so central differences are
+    exact up to the float32 rounding of the perturbed inputs)."""
+    torch = pytest.importorskip("torch")
+    import oracle
+    s = synth.Setup("gc", 5, 400.0, 8.0, 1e-3, 0.0, 3.0, 4, 9)
+    d = oracle.delay_table(*s.plan_args()[:7])
+    n_in = s.n_out + int(d.max())
+
+    class OracleDD(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, x, w):
+            ctx.save_for_backward(x, w)
+            return torch.from_numpy(oracle.forward_f32(d, x.numpy(), s.n_out, w.numpy()))
+
+        @staticmethod
+        def backward(ctx, g):
+            x, w = ctx.saved_tensors
+            gx = oracle.adjoint_f32(d, g.numpy(), n_in, w.numpy())
+            gw = oracle.wgrad_f32(d, g.numpy(), x.numpy())
+            return torch.from_numpy(gx), torch.from_numpy(gw)
+
+    gen = torch.Generator().manual_seed(3)
+    x = torch.randn(s.channels, n_in, dtype=torch.float64, generator=gen).float().double().requires_grad_()
+    w = torch.rand(s.channels, dtype=torch.float64, generator=gen).float().double().requires_grad_()
+    assert torch.autograd.gradcheck(OracleDD.apply, (x, w), eps=1e-3, atol=1e-4, rtol=1e-3)
