@@ -322,6 +322,8 @@ dd_status dd_stream_destroy(dd_stream_t st);
  * config name, time) and an existing entry for the same key is reused without
  * timing.  Allocates and frees its own device buffers; synchronises the
  * device.  *best_ms (nullable) receives the selected config's median time.
+ * A plan created while the environment variable DD_TUNE_DB names such a file
+ * starts with the choice recorded there for its device and geometry, if any.
  */
 dd_status dd_tune(dd_plan_t plan, double budget_s, const char* db_path, double* best_ms);
 

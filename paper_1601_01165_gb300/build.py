@@ -71,7 +71,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
                 logs.append(f.result())
     if todo or not os.path.exists(LIB):
         tmp = LIB + f".tmp{os.getpid()}"
-        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"],
+        r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-ldl"],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -87,6 +87,7 @@ using namespace dd;
 extern "C" dd_status dd_adjoint(dd_plan_t plan, const float* grad_out, int64_t go_row_stride, const float* w,
                                 float* grad_in, int64_t gi_row_stride, const float* in, int64_t in_row_stride,
                                 float* grad_w, void* stream) {
+  NvtxRange range("dd_adjoint");
   clear_error();
   if (!plan) return set_error(DD_ERR_ARG, "dd_adjoint: plan is NULL");
   if (plan->dtype != DD_F32_F32) return set_error(DD_ERR_UNSUPPORTED, "dd_adjoint: float32 plans only");

@@ -122,6 +122,7 @@ extern "C" dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, in
 
 extern "C" dd_status dd_batch_run(dd_batch_t b, const void* const* ins, const int64_t* in_strides,
                                   void* const* outs, const int64_t* out_strides, void* stream) {
+  NvtxRange range("dd_batch_run");
   clear_error();
   if (!b || !ins || !in_strides || !outs || !out_strides) return set_error(DD_ERR_ARG, "dd_batch_run: NULL argument");
   const size_t n = b->plans.size();

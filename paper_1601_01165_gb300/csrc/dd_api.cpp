@@ -113,6 +113,7 @@ extern "C" const char* dd_version(void) { return "libdd 0.1 (sm_103a)"; }
 
 extern "C" dd_status dd_forward(dd_plan_t plan, const void* in, int64_t in_row_stride, const float* w, void* out,
                                 int64_t out_row_stride, void* stream) {
+  NvtxRange range("dd_forward");
   clear_error();
   if (!plan) return set_error(DD_ERR_ARG, "dd_forward: plan is NULL");
   return forward_device(plan, in, in_row_stride, w, out, out_row_stride, static_cast<cudaStream_t>(stream), -1);
@@ -120,6 +121,7 @@ extern "C" dd_status dd_forward(dd_plan_t plan, const void* in, int64_t in_row_s
 
 extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_t in_row_stride,
                                      const float* host_w, void* host_out, int64_t out_row_stride, void* stream) {
+  NvtxRange range("dd_forward_host");
   clear_error();
   if (!plan || !host_in || !host_out) return set_error(DD_ERR_ARG, "dd_forward_host: NULL argument");
   if (in_row_stride < plan->n_in) return set_error(DD_ERR_SHAPE, "dd_forward_host: in_row_stride < n_in");

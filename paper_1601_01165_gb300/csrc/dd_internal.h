@@ -7,8 +7,17 @@
 #include <vector>
 
 #include "dd.h"
+#include "nvtx3/nvToolsExt.h"
 
 namespace dd {
+
+// NVTX range over one API call, shown by Nsight tools (no cost without one).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Forward kernel families.  NAIVE is the paper's "generically tuned" layout
 // (Section 5: one DM per thread, 1-D blocks, no explicit data reuse); STAGED is
@@ -48,6 +57,10 @@ struct FwdArgs {
   int64_t n_in;
   int* status;             // device error word
 };
+
+// Select the configuration recorded for this plan in the database named by
+// the DD_TUNE_DB environment variable, if there is one (tune.cpp).
+void apply_tune_db(dd_plan_s* plan);
 
 // TMW6 needs 16-byte aligned input rows of a multiple of 32 floats (128 bytes).
 bool tmw6_accepts(const void* in, int64_t in_stride);

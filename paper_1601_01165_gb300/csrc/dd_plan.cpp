@@ -296,6 +296,7 @@ extern "C" dd_status dd_plan(dd_plan_t* out, int32_t channels, double f_low_mhz,
     delete p;
     return st;
   }
+  apply_tune_db(p);
   *out = p;
   return DD_OK;
 }

@@ -197,6 +197,7 @@ using namespace dd;
 
 extern "C" dd_status dd_boxcar_snr(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
                                    dd_snr_result* result, float* grad, int64_t grad_stride, void* stream) {
+  NvtxRange range("dd_boxcar_snr");
   clear_error();
   dd_status st = boxcar_snr_check(x, row_stride, n_rows, n_cols, result, grad, grad_stride);
   if (st != DD_OK) return st;

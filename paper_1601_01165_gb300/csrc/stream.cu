@@ -72,6 +72,7 @@ extern "C" dd_status dd_stream_create(dd_stream_t* out, dd_plan_t plan, int64_t 
 }
 
 extern "C" dd_status dd_stream_push(dd_stream_t st, const void* chunk, void* out, int64_t* out_t0, void* stream) {
+  NvtxRange range("dd_stream_push");
   clear_error();
   if (!st || !chunk || !out) return set_error(DD_ERR_ARG, "dd_stream_push: NULL argument");
   cudaStream_t s = static_cast<cudaStream_t>(stream);

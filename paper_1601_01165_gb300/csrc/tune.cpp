@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -52,11 +53,24 @@ static bool db_lookup(const char* path, const std::string& key, std::string& cfg
   return found;
 }
 
+// A plan made while DD_TUNE_DB names a tuning database takes the choice
+// recorded there for its device and geometry, if any (no timing is done).
+void apply_tune_db(dd_plan_s* plan) {
+  const char* path = std::getenv("DD_TUNE_DB");
+  if (!path || !*path) return;
+  std::string name;
+  double ms = 0;
+  if (!db_lookup(path, tune_key(*plan), name, ms)) return;
+  for (size_t k = 0; k < plan->configs.size(); ++k)
+    if (plan->configs[k].name == name) plan->selected = (int)k;
+}
+
 }  // namespace dd
 
 using namespace dd;
 
 extern "C" dd_status dd_tune(dd_plan_t plan, double budget_s, const char* db_path, double* best_ms) {
+  NvtxRange range("dd_tune");
   clear_error();
   if (!plan) return set_error(DD_ERR_ARG, "dd_tune: plan is NULL");
   const std::string key = tune_key(*plan);

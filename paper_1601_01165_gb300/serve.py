@@ -165,6 +165,7 @@ class Server:
                     if act.pending is not None or k != act.next_chunk:
                         still.append((arr, name, k))
                         continue
+                    torch.cuda.nvtx.range_push(f"chunk {name}:{k}")
                     host = chunk_source(act.spec, k)
                     h = act.h_in
                     h.copy_(torch.from_numpy(np.ascontiguousarray(host)))
@@ -174,6 +175,7 @@ class Server:
                         act.h_out.copy_(act.d_out, non_blocking=True)
                         ev = torch.cuda.Event()
                         ev.record(act.cuda_stream)
+                    torch.cuda.nvtx.range_pop()
                     act.pending = (k, arr, t0, ev, h)
                     act.next_chunk += 1
                 ready = still

@@ -133,6 +133,12 @@ def test_tune_selects_and_records(dd, tmp_path):
     plan2 = dd.Plan.from_setup(s, "f32")
     name2, ms2 = plan2.tune(db_path=db)       # database hit: no timing
     assert name2 == name and abs(ms2 - rec["ms"]) < 1e-6
+    import os
+    os.environ["DD_TUNE_DB"] = db                 # plans made now start with the recorded choice
+    try:
+        assert dd.Plan.from_setup(s, "f32").selected == name
+    finally:
+        del os.environ["DD_TUNE_DB"]
     x = plan.alloc_input()
     x.normal_()
     assert torch.equal(plan.forward(x), plan2.forward(x))
