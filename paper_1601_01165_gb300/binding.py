@@ -39,13 +39,17 @@ def library_path() -> str:
 
 
 def load(build_if_missing: bool = True) -> ctypes.CDLL:
-    """Load libdd.so (building it first if it is missing and nvcc is present)."""
+    """Load libdd.so (building it first if it is missing and nvcc is present).
+    The environment variable DD_LIBRARY may name another build of the library
+    (the tests use it for the checked build)."""
     global _lib
     with _lock:
         if _lib is not None:
             return _lib
-        path = _build.LIB
+        path = os.environ.get("DD_LIBRARY") or _build.LIB
         if not os.path.exists(path):
+            if os.environ.get("DD_LIBRARY"):
+                raise RuntimeError(f"DD_LIBRARY names a missing file: {path}")
             if not build_if_missing:
                 raise RuntimeError(f"libdd.so is not built ({path}); run __graft_entry__.build()")
             _build.build()

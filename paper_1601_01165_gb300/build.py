@@ -19,6 +19,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libdd.so")
+# checked variant (-DDD_CHECKED): kernels record out-of-range indices in the
+# plan's status word instead of making the access; used by the tests
+BUILD_CHECKED = os.path.join(PKG, "_build_checked")
+LIB_CHECKED = os.path.join(BUILD_CHECKED, "libdd_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               f"-I{INCLUDE}", f"-I{CSRC}", "--expt-relaxed-constexpr"]
@@ -51,14 +55,17 @@ def _compile(nvcc: str, src: str, obj: str, extra: list[str], verbose: bool) -> 
     return r.stderr
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    """Compile every csrc/ unit for sm_103a and link libdd.so; returns its path."""
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None, checked: bool = False) -> str:
+    """Compile every csrc/ unit for sm_103a and link libdd.so (or, with
+    checked=True, libdd_checked.so built with -DDD_CHECKED); returns its path."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    out_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    extra = ["-DDD_CHECKED"] if checked else []
+    os.makedirs(out_dir, exist_ok=True)
     hdr = _headers_mtime()
     todo, objs = [], []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+        obj = os.path.join(out_dir, os.path.basename(src) + ".o")
         objs.append(obj)
         if force or verbose or not os.path.exists(obj) or \
                 os.path.getmtime(obj) < max(os.path.getmtime(src), hdr):
@@ -66,19 +73,19 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     logs = []
     if todo:
         with cf.ThreadPoolExecutor(max_workers=jobs or min(len(todo), os.cpu_count() or 4)) as ex:
-            futs = [ex.submit(_compile, nvcc, s, o, [], verbose) for s, o in todo]
+            futs = [ex.submit(_compile, nvcc, s, o, extra, verbose) for s, o in todo]
             for f in futs:
                 logs.append(f.result())
-    if todo or not os.path.exists(LIB):
-        tmp = LIB + f".tmp{os.getpid()}"
+    if todo or not os.path.exists(lib):
+        tmp = lib + f".tmp{os.getpid()}"
         r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda", "-ldl"],
                            capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
         sys.stderr.write("".join(logs))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":

@@ -115,6 +115,8 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
       const int64_t hi = t0 + nt + __ldg(a.delaysT + c * a.n_dm_pad + i0 + BD - 1);
       al = lo & ~(int64_t)(V - 1);
       ah = (hi + V - 1) & ~(int64_t)(V - 1);
+      // the span fits its shared-memory row and its input row
+      if (!DD_INDEX_OK(a.status, al >= 0 && ah - al <= pitch && ah <= a.in_stride)) ah = al + V;
     };
     uint32_t bytes = 0;
     for (int j = 0; j < cn; ++j) {
@@ -167,6 +169,7 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
       const int d0 = dl[0];
       const int64_t al = (t0 + d0) & ~(int64_t)(V - 1);
       const int base = (int)(t0 + d0 - al);  // row index of (DM i0, sample t0)
+      if (!DD_INDEX_OK(a.status, base >= 0 && base + dl[BD - 1] - d0 + BT <= pitch)) continue;
       float wc = 1.0f;
       if constexpr (WEIGHTED) wc = __ldg(a.w + c0 + j);
 #pragma unroll
@@ -255,6 +258,7 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
       const int64_t hi = t0 + nt + __ldg(a.delaysT + c * a.n_dm_pad + i0 + BD - 1);
       al = lo & ~(int64_t)(V - 1);
       ah = (hi + V - 1) & ~(int64_t)(V - 1);
+      if (!DD_INDEX_OK(a.status, al >= 0 && ah - al <= pitch && ah <= a.in_stride)) ah = al + V;
     };
     uint32_t bytes = 0;
     for (int j = 0; j < cn; ++j) {
@@ -306,6 +310,8 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
     const uint32_t* wp = reinterpret_cast<const uint32_t*>(row) + (off >> 2);
     const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(off & 3);
     uint32_t wv[KW + 1];
+    // the KW + 1 words stay inside the channel's shared-memory row
+    if (!DD_INDEX_OK(a.status, off >= 0 && (off >> 2) + KW + 1 <= pitch / 4)) wp = reinterpret_cast<const uint32_t*>(row);
 #pragma unroll
     for (int w = 0; w <= KW; ++w) wv[w] = wp[w];
 #pragma unroll

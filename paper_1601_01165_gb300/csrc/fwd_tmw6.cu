@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
     const int need = dsc.w;  // floats from the aligned start: shift + 32 + max offset
     const int lead = 4 * (c4 & 3);
     const int ng = (lead + need + 15) >> 4;  // 3..5
+    // the window's groups stay inside the slot and the tile's rows
+    if (!DD_INDEX_OK(a.status, need >= 32 && lead + need <= kSlot && lane + 2 < kQRows)) return true;
     const uint32_t col = tq + (uint32_t)(kSlot * sl);
     const uint32_t rb0 = rbase(lane), rb1 = rbase(lane + 1), rb2 = rbase(lane + 2);
     float v[16];
@@ -240,6 +242,9 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
       const int4 si = H.slot[q][set + k];
       const uint32_t bytes = (uint32_t)(word_a ? si.y : si.x) >> shift_a;
       const uint32_t col = tq + (uint32_t)(kSlot * (set + k));
+      // both trials' 32 columns stay inside the slot (warp-uniform)
+      if (!DD_INDEX_OK(a.status, (bytes & 0xffu) + 32 <= (uint32_t)kSlot && ((bytes >> 8) & 0xffu) + 32 <= (uint32_t)kSlot))
+        continue;
       float v0[32], v1[32];
       tmem_ld32(col + (bytes & 0xffu), v0);
       tmem_ld32(col + ((bytes >> 8) & 0xffu), v1);

@@ -64,11 +64,24 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 constexpr long long kWaitLimitCycles = 2000000000LL;
 
 // Device-side error codes written to the plan's status word.
-enum DeviceError : int { kDevOk = 0, kDevWaitTimeout = 1, kDevBadDescriptor = 2 };
+enum DeviceError : int { kDevOk = 0, kDevWaitTimeout = 1, kDevBadDescriptor = 2, kDevBadIndex = 3 };
 
 __device__ __forceinline__ void report_error(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
+
+// Checked builds (-DDD_CHECKED, used by the tests as a sanitizer stand-in):
+// an index outside its buffer records kDevBadIndex in the status word and the
+// caller skips the access; in normal builds the check compiles away.
+__device__ __forceinline__ bool index_ok(int* status, bool cond) {
+  if (!cond) report_error(status, kDevBadIndex);
+  return cond;
+}
+#ifdef DD_CHECKED
+#define DD_INDEX_OK(status, cond) ::dd::index_ok((status), (cond))
+#else
+#define DD_INDEX_OK(status, cond) true
+#endif
 
 }  // namespace dd
 
