@@ -79,6 +79,11 @@ dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const 
 // Shared-memory limit for one block (opt-in maximum on sm_103a).
 constexpr int kMaxSmemPerBlock = 227 * 1024;
 
+// The transposed delay table's rows hold n_dm rounded up to a multiple of
+// kDmPad trials (the padding repeats the last trial).  A block that reads the
+// delays of trials [i0, i0 + BD) stays inside its row only if BD divides kDmPad.
+constexpr int kDmPad = 64;
+
 // TMW6: the largest offset between a 6-trial group's first and last trial
 // that its Tensor Memory windows can hold.
 constexpr int kW6MaxOff = 31;

@@ -118,13 +118,14 @@ void free_plan_device(dd_plan_s* p) {
 }
 
 // Default configuration: the first valid entry of a preference list, in
-// the order measured on the Table 2 setups (Apertif float: TMW6 5.06 ms,
-// staged d32/t512 5.66 ms; LOFAR float: staged d32/t512 3.76 ms; Apertif
-// uint8: U8PK 4.25 ms); dd_tune replaces it with a measured choice.  TMW6 is
-// offered only where a 6-trial group's offsets fit its windows (Apertif, not
-// LOFAR).
-static const char* const kPrefsF32[] = {"tmw6_f32_d6_t4096", "staged_d32_t512_c4_s3", "staged_d8_t1024_c4_s3",
-                                        "staged_d16_t512_c8_s3", "staged_d16_t256_c8_s3", "naive_t256"};
+// the order measured on the Table 2 setups (Apertif float: TMW6 4.84 ms,
+// staged d32/t512/c8 4.87 ms; LOFAR float: staged d32/t512/c8 3.24 ms;
+// Apertif uint8: U8PK 2.97 ms); dd_tune replaces it with a measured choice.
+// TMW6 is offered only where a 6-trial group's offsets fit its windows
+// (Apertif, not LOFAR).
+static const char* const kPrefsF32[] = {"tmw6_f32_d6_t4096",     "staged_d32_t512_c8_s2", "staged_d8_t1024_c4_s3",
+                                        "staged_d32_t384_c4_s3", "staged_d16_t512_c8_s3", "staged_d16_t256_c8_s3",
+                                        "naive_t256"};
 static const char* const kPrefsU8[] = {"u8pk_w8x1_d2_c16_st4", "u8pk_w8x1_d4_c16_st3", "staged_d8_t1024_c4_s3",
                                        "staged_d16_t512_c8_s3", "naive_t256"};
 
@@ -150,7 +151,7 @@ static int fallback_config(const dd_plan_s& p) { return preferred(p, true); }
 dd_status finish_plan(dd_plan_s* p) {
   p->max_delay = *std::max_element(p->delays.begin(), p->delays.end());
   p->n_in = p->n_out + p->max_delay;
-  p->n_dm_pad = (p->n_dm + 63) / 64 * 64;
+  p->n_dm_pad = (p->n_dm + kDmPad - 1) / kDmPad * kDmPad;
 
   if (cudaGetDevice(&p->device) != cudaSuccess) return set_cuda_error("dd_plan: cudaGetDevice");
   // transposed, padded copy: [C][n_dm_pad], trials past n_dm repeat the last

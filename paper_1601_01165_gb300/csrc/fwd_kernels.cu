@@ -78,6 +78,70 @@ __device__ __forceinline__ void init_stage_bars(uint64_t* bars, int stages) {
   __syncthreads();
 }
 
+// Warp 0 of a STAGED or U8PK block stages the input, one lane per channel:
+// chunk k (channels [k CC, k CC + CC)) goes to one stage, lane j copying the
+// span of channel k CC + j and its BD delays.  A lane reads its channel's
+// first and last trial delays one chunk before it stages that chunk
+// (stage_fetch), so the delay-table latency stays off the block's path.
+template <int BD, int CC>
+__device__ __forceinline__ void stage_fetch(const FwdArgs& a, int i0, int k, int lane, int32_t& dlo, int32_t& dhi) {
+  static_assert(CC <= 32, "one lane per channel of a chunk");
+  const int c = k * CC + lane;
+  if (lane < CC && c < a.C) {
+    const int32_t* col = a.delaysT + (int64_t)c * a.n_dm_pad + i0;
+    dlo = __ldg(col);
+    dhi = __ldg(col + BD - 1);
+  }
+}
+
+// Warp 0, all lanes: stage chunk k into stage s (barrier `bar`) from the
+// delays stage_fetch read.  Each span covers samples [t0 + dlo, t0 + nt +
+// dhi) of its channel row, widened to 16-byte boundaries.
+template <typename Tin, int BD, int CC>
+__device__ __forceinline__ void stage_issue(const FwdArgs& a, int pitch, int64_t t0, int nt, int i0, int k, int s,
+                                            int lane, int32_t dlo, int32_t dhi, uint64_t* bar, Tin* sin,
+                                            int32_t* sdel) {
+  constexpr int V = 16 / (int)sizeof(Tin);
+  const int c = k * CC + lane;
+  const bool mine = lane < CC && c < a.C;
+  int64_t al = 0, ah = 0;
+  if (mine) {
+    al = (t0 + dlo) & ~(int64_t)(V - 1);
+    ah = (t0 + nt + dhi + V - 1) & ~(int64_t)(V - 1);
+    // the span fits its shared-memory row and its input row
+    if (!DD_INDEX_OK(a.status, al >= 0 && ah - al <= pitch && ah <= a.in_stride)) al = 0, ah = V;
+  }
+  const uint32_t bytes = mine ? (uint32_t)((ah - al) * (int64_t)sizeof(Tin)) + BD * 4 : 0u;
+  const uint32_t total = __reduce_add_sync(0xffffffffu, bytes);
+  if (lane == 0) mbar_arrive_expect_tx(bar, total);
+  __syncwarp();
+  if (mine) {
+    bulk_g2s(sin + (size_t)(s * CC + lane) * pitch, static_cast<const Tin*>(a.in) + (int64_t)c * a.in_stride + al,
+             (uint32_t)((ah - al) * (int64_t)sizeof(Tin)), bar);
+    bulk_g2s(sdel + (s * CC + lane) * BD, a.delaysT + (int64_t)c * a.n_dm_pad + i0, BD * 4, bar);
+  }
+}
+
+// Warp 0: stage the first min(STAGES, nchunks) chunks and read the delays of
+// chunk STAGES into (dlo, dhi).
+template <typename Tin, int BD, int CC, int STAGES>
+__device__ __forceinline__ void stage_prologue(const FwdArgs& a, int pitch, int64_t t0, int nt, int i0, int nchunks,
+                                               uint32_t kb, int lane, uint64_t* bars, Tin* sin, int32_t* sdel,
+                                               int32_t& dlo, int32_t& dhi) {
+  int32_t plo[STAGES], phi[STAGES];
+#pragma unroll
+  for (int j = 0; j < STAGES; ++j) {
+    plo[j] = phi[j] = 0;
+    stage_fetch<BD, CC>(a, i0, j, lane, plo[j], phi[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < STAGES; ++j) {
+    const int s = (int)((kb + (uint32_t)j) % STAGES);
+    if (j < nchunks) stage_issue<Tin, BD, CC>(a, pitch, t0, nt, i0, j, s, lane, plo[j], phi[j], &bars[s], sin, sdel);
+  }
+  stage_fetch<BD, CC>(a, i0, STAGES, lane, dlo, dhi);
+}
+
 // One tile: DM trials [by*BD, by*BD + BD) x samples [bx*BT, bx*BT + BT).
 // `kbase` counts the chunks this block consumed before the tile, so the
 // stage barriers' phases carry on across the tiles of a persistent block.
@@ -91,13 +155,14 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
   constexpr int DPW = BD / NW;
   constexpr int SPL = BT / 32;
   static_assert(BD % NW == 0 && BT % 32 == 0 && BD % 4 == 0, "tile shape");
+  // a block's delay slice [i0, i0 + BD) must stay inside the padded row
+  static_assert(kDmPad % BD == 0, "BD must divide the trial padding");
   static_assert(STAGES * 8 <= kStBarBytes, "barrier area");
 
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
   Tin* sin = reinterpret_cast<Tin*>(smem_raw + kStBarBytes);
   int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes + (size_t)STAGES * CC * pitch * sizeof(Tin));
 
-  const Tin* __restrict__ in = static_cast<const Tin*>(a.in);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t t0 = bx * BT;
   const int i0 = by * BD;
@@ -105,39 +170,10 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
   const int nchunks = (a.C + CC - 1) / CC;
   const uint32_t kb = kbase;
 
-  // Producer (thread 0): stage chunk k (channels [k*CC, k*CC + CC)) into stage (kb + k) % STAGES.
-  auto issue = [&](int k) {
-    const int s = (int)((kb + (uint32_t)k) % STAGES);
-    const int c0 = k * CC;
-    const int cn = min(CC, a.C - c0);
-    auto span = [&](int64_t c, int64_t& al, int64_t& ah) {
-      const int64_t lo = t0 + __ldg(a.delaysT + c * a.n_dm_pad + i0);
-      const int64_t hi = t0 + nt + __ldg(a.delaysT + c * a.n_dm_pad + i0 + BD - 1);
-      al = lo & ~(int64_t)(V - 1);
-      ah = (hi + V - 1) & ~(int64_t)(V - 1);
-      // the span fits its shared-memory row and its input row
-      if (!DD_INDEX_OK(a.status, al >= 0 && ah - al <= pitch && ah <= a.in_stride)) ah = al + V;
-    };
-    uint32_t bytes = 0;
-    for (int j = 0; j < cn; ++j) {
-      int64_t al, ah;
-      span(c0 + j, al, ah);
-      bytes += (uint32_t)((ah - al) * (int64_t)sizeof(Tin)) + BD * 4;
-    }
-    mbar_arrive_expect_tx(&bars[s], bytes);
-    for (int j = 0; j < cn; ++j) {
-      const int64_t c = c0 + j;
-      int64_t al, ah;
-      span(c, al, ah);
-      bulk_g2s(sin + (size_t)(s * CC + j) * pitch, in + c * a.in_stride + al,
-               (uint32_t)((ah - al) * (int64_t)sizeof(Tin)), &bars[s]);
-      bulk_g2s(sdel + (s * CC + j) * BD, a.delaysT + c * a.n_dm_pad + i0, BD * 4, &bars[s]);
-    }
-  };
-
-  if (tid == 0) {
-    for (int k = 0; k < min(STAGES, nchunks); ++k) issue(k);
-  }
+  // Warp 0 stages the chunks; (dlo, dhi) hold its lanes' delays of the next chunk to stage.
+  int32_t dlo = 0, dhi = 0;
+  if (warp == 0)
+    stage_prologue<Tin, BD, CC, STAGES>(a, pitch, t0, nt, i0, nchunks, kb, lane, bars, sin, sdel, dlo, dhi);
 
   Tacc acc[DPW][SPL];
 #pragma unroll
@@ -159,7 +195,11 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
       }
       return false;
     }
-    if (tid == 0 && k >= 1 && k - 1 + STAGES < nchunks) issue(k - 1 + STAGES);
+    if (warp == 0 && k >= 1 && k - 1 + STAGES < nchunks) {
+      const int kn = k - 1 + STAGES, sn = (int)((kb + (uint32_t)kn) % STAGES);
+      stage_issue<Tin, BD, CC>(a, pitch, t0, nt, i0, kn, sn, lane, dlo, dhi, &bars[sn], sin, sdel);
+      stage_fetch<BD, CC>(a, i0, kn + 1, lane, dlo, dhi);
+    }
 
     const int c0 = k * CC;
     const int cn = min(CC, a.C - c0);
@@ -213,17 +253,20 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
 }
 
 // ------------------------------------------------------------------- U8PK
-// uint8 -> int32 with packed 16-bit accumulation.  The block stages byte spans
+// uint8 -> int32 with packed accumulation.  The block stages byte spans
 // exactly like STAGED.  A warp owns DPW DM trials x 32 lanes x 28 samples (7
 // words; odd, so the lanes' word loads hit distinct banks).  Per channel and
-// trial a lane loads 8 words covering its 28 samples at the trial's delay,
+// trial a lane loads 8 words covering its 28 samples at the trial's delay and
 // aligns them with one byte permute whose selector is the same for the whole
-// warp (the delay modulo 4), splits each aligned word into its even and odd
-// samples as 16-bit lanes, and adds two channels at a time into packed 16-bit
-// sums (one 3-input integer add per 4 samples and 2 channels).  256 channels
-// of 8-bit samples fit a 16-bit lane exactly (256 * 255 < 65536), so every
-// 256 channels the packed sums are added into int32 totals and cleared: the
-// result is the exact integer sum.
+// warp (the delay modulo 4).  For each aligned word x = s0 + 2^8 s1 + 2^16 s2
+// + 2^24 s3 it keeps two sums: A, the words themselves modulo 2^32, and B, the
+// odd samples s1, s3 as two 16-bit lanes.  Over at most 256 channels every
+// per-sample sum S_k stays below 2^16 (256 * 255 < 65536), so B holds S1 and
+// S3 exactly and A - 2^8 S1 - 2^24 S3 = S0 + 2^16 S2 (mod 2^32) gives S0 and
+// S2; every 256 channels the four sums are added into int32 totals and A, B
+// cleared, so the result is the exact integer sum.  The sums are formed with
+// integer multiply-adds by a run-time 1 so that they issue to the FMA pipe,
+// leaving the ALU pipe to the byte permutes (two per word and channel).
 template <int WD, int WT, int DPW, int CC, int STAGES>
 __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t bx, int by, uint32_t& kbase,
                                           unsigned char* smem_raw) {
@@ -234,13 +277,12 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
   constexpr int BD = WD * DPW;
   constexpr int BT = 32 * SPL * WT;
   static_assert(BD % 4 == 0 && BT % 16 == 0, "tile shape");
-
+  static_assert(kDmPad % BD == 0, "BD must divide the trial padding");
   static_assert(STAGES * 8 <= kStBarBytes, "barrier area");
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
   uint8_t* sin = smem_raw + kStBarBytes;
   int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes + (size_t)STAGES * CC * pitch);
 
-  const uint8_t* __restrict__ in = static_cast<const uint8_t*>(a.in);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wd = warp % WD, wt = warp / WD;
   const int64_t t0 = bx * BT;
@@ -249,42 +291,16 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
   const int nchunks = (a.C + CC - 1) / CC;
   const uint32_t kb = kbase;
 
-  auto issue = [&](int k) {
-    const int s = (int)((kb + (uint32_t)k) % STAGES);
-    const int c0 = k * CC;
-    const int cn = min(CC, a.C - c0);
-    auto span = [&](int64_t c, int64_t& al, int64_t& ah) {
-      const int64_t lo = t0 + __ldg(a.delaysT + c * a.n_dm_pad + i0);
-      const int64_t hi = t0 + nt + __ldg(a.delaysT + c * a.n_dm_pad + i0 + BD - 1);
-      al = lo & ~(int64_t)(V - 1);
-      ah = (hi + V - 1) & ~(int64_t)(V - 1);
-      if (!DD_INDEX_OK(a.status, al >= 0 && ah - al <= pitch && ah <= a.in_stride)) ah = al + V;
-    };
-    uint32_t bytes = 0;
-    for (int j = 0; j < cn; ++j) {
-      int64_t al, ah;
-      span(c0 + j, al, ah);
-      bytes += (uint32_t)(ah - al) + BD * 4;
-    }
-    mbar_arrive_expect_tx(&bars[s], bytes);
-    for (int j = 0; j < cn; ++j) {
-      const int64_t c = c0 + j;
-      int64_t al, ah;
-      span(c, al, ah);
-      bulk_g2s(sin + (size_t)(s * CC + j) * pitch, in + c * a.in_stride + al, (uint32_t)(ah - al), &bars[s]);
-      bulk_g2s(sdel + (s * CC + j) * BD, a.delaysT + c * a.n_dm_pad + i0, BD * 4, &bars[s]);
-    }
-  };
-  if (tid == 0) {
-    for (int k = 0; k < min(STAGES, nchunks); ++k) issue(k);
-  }
+  int32_t dlo = 0, dhi = 0;  // warp 0: its lanes' delays of the next chunk to stage
+  if (warp == 0)
+    stage_prologue<uint8_t, BD, CC, STAGES>(a, pitch, t0, nt, i0, nchunks, kb, lane, bars, sin, sdel, dlo, dhi);
 
-  uint32_t pe[DPW][KW], po[DPW][KW];  // packed 16-bit sums: even / odd samples of each word
+  uint32_t ra[DPW][KW], rb[DPW][KW];  // A and B of each word (see above)
   int32_t tot[DPW][SPL];
 #pragma unroll
   for (int m = 0; m < DPW; ++m) {
 #pragma unroll
-    for (int w = 0; w < KW; ++w) pe[m][w] = po[m][w] = 0u;
+    for (int w = 0; w < KW; ++w) ra[m][w] = rb[m][w] = 0u;
 #pragma unroll
     for (int q = 0; q < SPL; ++q) tot[m][q] = 0;
   }
@@ -293,12 +309,21 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
     for (int m = 0; m < DPW; ++m)
 #pragma unroll
       for (int w = 0; w < KW; ++w) {
-        tot[m][4 * w + 0] += (int32_t)(pe[m][w] & 0xffffu);
-        tot[m][4 * w + 2] += (int32_t)(pe[m][w] >> 16);
-        tot[m][4 * w + 1] += (int32_t)(po[m][w] & 0xffffu);
-        tot[m][4 * w + 3] += (int32_t)(po[m][w] >> 16);
-        pe[m][w] = po[m][w] = 0u;
+        const uint32_t s1 = rb[m][w] & 0xffffu, s3 = rb[m][w] >> 16;
+        const uint32_t s02 = ra[m][w] - (s1 << 8) - (s3 << 24);  // S0 + 2^16 S2
+        tot[m][4 * w + 0] += (int32_t)(s02 & 0xffffu);
+        tot[m][4 * w + 1] += (int32_t)s1;
+        tot[m][4 * w + 2] += (int32_t)(s02 >> 16);
+        tot[m][4 * w + 3] += (int32_t)s3;
+        ra[m][w] = rb[m][w] = 0u;
       }
+  };
+  // x + y * one with one == 1 at run time: an integer multiply-add (FMA pipe)
+  const uint32_t one = a.C > 0 ? 1u : 0u;
+  auto madd = [](uint32_t x, uint32_t y, uint32_t m) {
+    uint32_t d;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(y), "r"(m), "r"(x));
+    return d;
   };
   // aligned words of (trial slot m, channel row j of stage s) -> x[KW]
   auto aligned = [&](int s, int j, int m, uint32_t (&x)[KW]) {
@@ -331,7 +356,11 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
       }
       return false;
     }
-    if (tid == 0 && k >= 1 && k - 1 + STAGES < nchunks) issue(k - 1 + STAGES);
+    if (warp == 0 && k >= 1 && k - 1 + STAGES < nchunks) {
+      const int kn = k - 1 + STAGES, sn = (int)((kb + (uint32_t)kn) % STAGES);
+      stage_issue<uint8_t, BD, CC>(a, pitch, t0, nt, i0, kn, sn, lane, dlo, dhi, &bars[sn], sin, sdel);
+      stage_fetch<BD, CC>(a, i0, kn + 1, lane, dlo, dhi);
+    }
     const int cn = min(CC, a.C - k * CC);
     int j = 0;
     for (; j + 1 < cn; j += 2) {
@@ -346,8 +375,8 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
         aligned(s, j + 1, m, x1);
 #pragma unroll
         for (int w = 0; w < KW; ++w) {
-          pe[m][w] += __byte_perm(x0[w], 0u, 0x4240u) + __byte_perm(x1[w], 0u, 0x4240u);
-          po[m][w] += __byte_perm(x0[w], 0u, 0x4341u) + __byte_perm(x1[w], 0u, 0x4341u);
+          ra[m][w] = madd(madd(ra[m][w], x0[w], one), x1[w], one);
+          rb[m][w] = madd(madd(rb[m][w], __byte_perm(x0[w], 0u, 0x4341u), one), __byte_perm(x1[w], 0u, 0x4341u), one);
         }
       }
       since_flush += 2;
@@ -363,8 +392,8 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
         aligned(s, j, m, x0);
 #pragma unroll
         for (int w = 0; w < KW; ++w) {
-          pe[m][w] += __byte_perm(x0[w], 0u, 0x4240u);
-          po[m][w] += __byte_perm(x0[w], 0u, 0x4341u);
+          ra[m][w] = madd(ra[m][w], x0[w], one);
+          rb[m][w] = madd(rb[m][w], __byte_perm(x0[w], 0u, 0x4341u), one);
         }
       }
       since_flush += 1;
@@ -437,7 +466,10 @@ static cudaError_t launch_staged_t(const TileConfig& cfg, const FwdArgs& a, cuda
   X(8, 512, 8, 3)            \
   X(8, 1024, 4, 3)           \
   X(32, 512, 4, 3)           \
-  X(64, 256, 4, 3)
+  X(64, 256, 4, 3)           \
+  X(32, 512, 2, 4)           \
+  X(32, 512, 8, 2)           \
+  X(32, 384, 4, 3)
 
 #define DD_U8PK_CASES(X) \
   X(8, 1, 2, 16, 4)      \
