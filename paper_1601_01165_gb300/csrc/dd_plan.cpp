@@ -119,15 +119,15 @@ void free_plan_device(dd_plan_s* p) {
 
 // Default configuration: the first valid entry of a preference list, in
 // the order measured on the Table 2 setups (Apertif float: TMW6 4.84 ms,
-// staged d32/t512/c8 4.87 ms; LOFAR float: staged d32/t512/c8 3.24 ms;
-// Apertif uint8: U8PK 2.97 ms); dd_tune replaces it with a measured choice.
-// TMW6 is offered only where a 6-trial group's offsets fit its windows
-// (Apertif, not LOFAR).
-static const char* const kPrefsF32[] = {"tmw6_f32_d6_t4096",     "staged_d32_t512_c8_s2", "staged_d8_t1024_c4_s3",
-                                        "staged_d32_t384_c4_s3", "staged_d16_t512_c8_s3", "staged_d16_t256_c8_s3",
+// staged d8/t1024 4.94 ms; LOFAR float: staged d8/t1024 3.19 ms, d32/t512/c8
+// 3.13 ms; Apertif uint8: U8PK c32 2.70 ms); dd_tune replaces it with a
+// measured choice.  TMW6 is offered only where a 6-trial group's offsets fit
+// its windows (Apertif, not LOFAR).
+static const char* const kPrefsF32[] = {"tmw6_f32_d6_t4096",     "staged_d8_t1024_c4_s3", "staged_d16_t512_c8_s3",
+                                        "staged_d32_t512_c8_s2", "staged_d32_t384_c4_s3", "staged_d16_t256_c8_s3",
                                         "naive_t256"};
-static const char* const kPrefsU8[] = {"u8pk_w8x1_d2_c16_st4", "u8pk_w8x1_d4_c16_st3", "staged_d8_t1024_c4_s3",
-                                       "staged_d16_t512_c8_s3", "naive_t256"};
+static const char* const kPrefsU8[] = {"u8pk_w8x1_d2_c32_st3", "u8pk_w8x1_d2_c16_st4", "u8pk_w8x1_d4_c16_st3",
+                                       "staged_d16_t512_c8_s3", "staged_d8_t1024_c4_s3", "naive_t256"};
 
 static int preferred(const dd_plan_s& p, bool staged_only) {
   const bool u8 = p.dtype == DD_U8_I32;

@@ -62,48 +62,68 @@ __global__ void __launch_bounds__(256) fwd_naive_kernel(FwdArgs a) {
 
 // Shared-memory layout of the staged kernels: kStBarBytes of mbarriers, then
 // [STAGES][CC][pitch] input spans (Tin) and [STAGES][CC][BD] int32 delay
-// slices.  The barriers come first so that a persistent block can work on
-// tiles of beams whose pitches differ.
+// slices.
 constexpr int kStBarBytes = 128;
 template <typename Tin>
 __host__ __device__ constexpr int staged_smem_bytes(int stages, int cc, int bd, int pitch) {
   return kStBarBytes + stages * cc * pitch * (int)sizeof(Tin) + stages * cc * bd * 4;
 }
 
-__device__ __forceinline__ void init_stage_bars(uint64_t* bars, int stages) {
+// The stage barriers: full[s] completes when stage s's copies have landed
+// (one arrival per copying warp with the bytes that warp copies, then the
+// bytes); empty[s] when every warp of the block has finished reading it (one
+// arrival per warp).  Warps synchronise only through these, never block-wide
+// inside the channel loop.
+template <int STAGES>
+struct StageBars {
+  uint64_t full[STAGES];
+  uint64_t empty[STAGES];
+};
+
+template <int STAGES>
+__device__ __forceinline__ StageBars<STAGES>& init_stage_bars(unsigned char* smem_raw, int warps, int copiers) {
+  static_assert(sizeof(StageBars<STAGES>) <= kStBarBytes, "barrier area");
+  StageBars<STAGES>& B = *reinterpret_cast<StageBars<STAGES>*>(smem_raw);
   if (threadIdx.x == 0) {
-    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&B.full[s], (uint32_t)copiers);
+      mbar_init(&B.empty[s], (uint32_t)warps);
+    }
     fence_mbar_init();
   }
   __syncthreads();
+  return B;
 }
 
-// Warp 0 of a STAGED or U8PK block stages the input, one lane per channel:
-// chunk k (channels [k CC, k CC + CC)) goes to one stage, lane j copying the
-// span of channel k CC + j and its BD delays.  A lane reads its channel's
-// first and last trial delays one chunk before it stages that chunk
-// (stage_fetch), so the delay-table latency stays off the block's path.
+// The warps of a STAGED or U8PK block copy their own input: chunk k
+// (channels [k CC, k CC + CC)) goes to stage k % STAGES, one lane per slot j
+// (the span of channel k CC + j and its BD delays).  With SPREAD every warp
+// copies part of each chunk (lane l of warp w takes slot w + NW l), so no warp
+// carries all the copies; without it warp 0 copies everything (lane l takes
+// slot l).  U8PK, which has few shared loads per add, runs fastest spread;
+// STAGED, bound by shared-memory bandwidth, with warp 0 alone.  A lane reads
+// its channel's first and last trial delays one chunk before it stages that
+// chunk (stage_fetch), so the delay-table latency stays off the warp's path.
 template <int BD, int CC>
-__device__ __forceinline__ void stage_fetch(const FwdArgs& a, int i0, int k, int lane, int32_t& dlo, int32_t& dhi) {
-  static_assert(CC <= 32, "one lane per channel of a chunk");
-  const int c = k * CC + lane;
-  if (lane < CC && c < a.C) {
+__device__ __forceinline__ void stage_fetch(const FwdArgs& a, int i0, int k, int slot, int32_t& dlo, int32_t& dhi) {
+  const int c = k * CC + slot;
+  if (slot < CC && c < a.C) {
     const int32_t* col = a.delaysT + (int64_t)c * a.n_dm_pad + i0;
     dlo = __ldg(col);
     dhi = __ldg(col + BD - 1);
   }
 }
 
-// Warp 0, all lanes: stage chunk k into stage s (barrier `bar`) from the
-// delays stage_fetch read.  Each span covers samples [t0 + dlo, t0 + nt +
-// dhi) of its channel row, widened to 16-byte boundaries.
+// All lanes of a warp: stage the warp's slots of chunk k into stage s
+// (barrier `bar`) from the delays stage_fetch read.  Each span covers samples
+// [t0 + dlo, t0 + nt + dhi) of its channel row, widened to 16-byte boundaries.
 template <typename Tin, int BD, int CC>
 __device__ __forceinline__ void stage_issue(const FwdArgs& a, int pitch, int64_t t0, int nt, int i0, int k, int s,
-                                            int lane, int32_t dlo, int32_t dhi, uint64_t* bar, Tin* sin,
+                                            int slot, int lane, int32_t dlo, int32_t dhi, uint64_t* bar, Tin* sin,
                                             int32_t* sdel) {
   constexpr int V = 16 / (int)sizeof(Tin);
-  const int c = k * CC + lane;
-  const bool mine = lane < CC && c < a.C;
+  const int c = k * CC + slot;
+  const bool mine = slot < CC && c < a.C;
   int64_t al = 0, ah = 0;
   if (mine) {
     al = (t0 + dlo) & ~(int64_t)(V - 1);
@@ -116,39 +136,98 @@ __device__ __forceinline__ void stage_issue(const FwdArgs& a, int pitch, int64_t
   if (lane == 0) mbar_arrive_expect_tx(bar, total);
   __syncwarp();
   if (mine) {
-    bulk_g2s(sin + (size_t)(s * CC + lane) * pitch, static_cast<const Tin*>(a.in) + (int64_t)c * a.in_stride + al,
+    bulk_g2s(sin + (size_t)(s * CC + slot) * pitch, static_cast<const Tin*>(a.in) + (int64_t)c * a.in_stride + al,
              (uint32_t)((ah - al) * (int64_t)sizeof(Tin)), bar);
-    bulk_g2s(sdel + (s * CC + lane) * BD, a.delaysT + (int64_t)c * a.n_dm_pad + i0, BD * 4, bar);
+    bulk_g2s(sdel + (s * CC + slot) * BD, a.delaysT + (int64_t)c * a.n_dm_pad + i0, BD * 4, bar);
   }
 }
 
-// Warp 0: stage the first min(STAGES, nchunks) chunks and read the delays of
-// chunk STAGES into (dlo, dhi).
-template <typename Tin, int BD, int CC, int STAGES>
-__device__ __forceinline__ void stage_prologue(const FwdArgs& a, int pitch, int64_t t0, int nt, int i0, int nchunks,
-                                               uint32_t kb, int lane, uint64_t* bars, Tin* sin, int32_t* sdel,
-                                               int32_t& dlo, int32_t& dhi) {
-  int32_t plo[STAGES], phi[STAGES];
+// A copying warp's side of the pipeline: `kn` is the next chunk it stages
+// and (dlo, dhi) its lanes' delays for it.
+template <typename Tin, int BD, int CC, int STAGES, int NW, bool SPREAD>
+struct Stager {
+  static_assert(STAGES >= 2, "chunk k + 1 is staged while chunk k is read");
+  static_assert(CC <= (SPREAD ? 32 * NW : 32), "one lane per slot of a chunk");
+  static constexpr int kCopiers = SPREAD ? NW : 1;  // warps that copy
+  const FwdArgs& a;
+  int pitch;
+  int64_t t0;
+  int nt, i0, nchunks, warp, lane;
+  StageBars<STAGES>& B;
+  Tin* sin;
+  int32_t* sdel;
+  int kn = 0;
+  int32_t dlo = 0, dhi = 0;
+
+  // does this warp copy, and which chunk slot does this lane copy
+  __device__ __forceinline__ bool copies() const { return SPREAD || warp == 0; }
+  __device__ __forceinline__ int slot() const { return SPREAD ? warp + NW * lane : lane; }
+
+  // Stage the first min(STAGES, nchunks) chunks (their stages start free),
+  // reading all their delays at once.
+  __device__ __forceinline__ void prologue() {
+    int32_t plo[STAGES], phi[STAGES];
 #pragma unroll
-  for (int j = 0; j < STAGES; ++j) {
-    plo[j] = phi[j] = 0;
-    stage_fetch<BD, CC>(a, i0, j, lane, plo[j], phi[j]);
-  }
+    for (int j = 0; j < STAGES; ++j) {
+      plo[j] = phi[j] = 0;
+      stage_fetch<BD, CC>(a, i0, j, slot(), plo[j], phi[j]);
+    }
 #pragma unroll
-  for (int j = 0; j < STAGES; ++j) {
-    const int s = (int)((kb + (uint32_t)j) % STAGES);
-    if (j < nchunks) stage_issue<Tin, BD, CC>(a, pitch, t0, nt, i0, j, s, lane, plo[j], phi[j], &bars[s], sin, sdel);
+    for (int j = 0; j < STAGES; ++j)
+      if (j < nchunks)
+        stage_issue<Tin, BD, CC>(a, pitch, t0, nt, i0, j, j, slot(), lane, plo[j], phi[j], &B.full[j], sin, sdel);
+    kn = min(STAGES, nchunks);
+    stage_fetch<BD, CC>(a, i0, STAGES, slot(), dlo, dhi);
   }
-  stage_fetch<BD, CC>(a, i0, STAGES, lane, dlo, dhi);
+
+  // Called by a copying warp before it consumes chunk k: stage, in order, its part of every chunk
+  // up to k + STAGES - 1 whose stage every warp has released (chunk kn's stage
+  // is free once chunk kn - STAGES is released).  Chunks k and k + 1 must be
+  // staged by now, so their stages are waited for (bounded; this keeps at
+  // least one chunk of copies ahead of the sums); later ones are only staged
+  // if already free.  False on a timeout.
+  __device__ __forceinline__ bool ahead(int k) {
+    const int upto = min(nchunks, k + STAGES);
+    while (kn < upto) {
+      const int s = kn % STAGES;
+      const uint32_t par = (uint32_t)(((kn - STAGES) / STAGES) & 1);
+      if (!__any_sync(0xffffffffu, mbar_test_wait(&B.empty[s], par))) {
+        if (kn > k + 1) break;  // try again at the next chunk
+        if (!__any_sync(0xffffffffu, mbar_wait_bounded(&B.empty[s], par, kWaitLimitCycles))) return false;
+      }
+      stage_issue<Tin, BD, CC>(a, pitch, t0, nt, i0, kn, s, slot(), lane, dlo, dhi, &B.full[s], sin, sdel);
+      stage_fetch<BD, CC>(a, i0, kn + 1, slot(), dlo, dhi);
+      ++kn;
+    }
+    return true;
+  }
+
+  // Before the block reuses the stages or leaves: no copy may still be in
+  // flight (after a timeout some staged chunks were never consumed).
+  __device__ __forceinline__ void drain() {
+    if (lane == 0)
+      for (int kk = max(0, kn - STAGES); kk < kn; ++kk)
+        (void)mbar_wait_bounded(&B.full[kk % STAGES], (uint32_t)((kk / STAGES) & 1), kWaitLimitCycles);
+    __syncwarp();
+  }
+};
+
+// Every warp: wait for chunk k's stage to be full (bounded, warp-uniform).
+template <int STAGES>
+__device__ __forceinline__ bool stage_wait_full(StageBars<STAGES>& B, int k) {
+  return __all_sync(0xffffffffu, mbar_wait_bounded(&B.full[k % STAGES], (uint32_t)((k / STAGES) & 1), kWaitLimitCycles));
+}
+
+// Every warp, after reading chunk k's stage: release it.
+template <int STAGES>
+__device__ __forceinline__ void stage_release(StageBars<STAGES>& B, int k, int lane) {
+  __syncwarp();
+  if (lane == 0) mbar_arrive(&B.empty[k % STAGES]);
 }
 
 // One tile: DM trials [by*BD, by*BD + BD) x samples [bx*BT, bx*BT + BT).
-// `kbase` counts the chunks this block consumed before the tile, so the
-// stage barriers' phases carry on across the tiles of a persistent block.
-// Returns false (on every thread) if a bounded wait expired.
 template <typename Tin, bool WEIGHTED, int BD, int BT, int CC, int STAGES>
-__device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t bx, int by, uint32_t& kbase,
-                                            unsigned char* smem_raw) {
+__global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
   using Tacc = typename AccOf<Tin>::type;
   constexpr int V = 16 / (int)sizeof(Tin);  // elements per 16 bytes
   constexpr int NW = 8;
@@ -157,23 +236,21 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
   static_assert(BD % NW == 0 && BT % 32 == 0 && BD % 4 == 0, "tile shape");
   // a block's delay slice [i0, i0 + BD) must stay inside the padded row
   static_assert(kDmPad % BD == 0, "BD must divide the trial padding");
-  static_assert(STAGES * 8 <= kStBarBytes, "barrier area");
 
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  using Pipe = Stager<Tin, BD, CC, STAGES, NW, false>;
+  StageBars<STAGES>& B = init_stage_bars<STAGES>(smem_raw, NW, Pipe::kCopiers);
   Tin* sin = reinterpret_cast<Tin*>(smem_raw + kStBarBytes);
   int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes + (size_t)STAGES * CC * pitch * sizeof(Tin));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t t0 = bx * BT;
-  const int i0 = by * BD;
+  const int64_t t0 = (int64_t)blockIdx.x * BT;
+  const int i0 = blockIdx.y * BD;
   const int nt = (int)min((int64_t)BT, a.n_out - t0);
   const int nchunks = (a.C + CC - 1) / CC;
-  const uint32_t kb = kbase;
 
-  // Warp 0 stages the chunks; (dlo, dhi) hold its lanes' delays of the next chunk to stage.
-  int32_t dlo = 0, dhi = 0;
-  if (warp == 0)
-    stage_prologue<Tin, BD, CC, STAGES>(a, pitch, t0, nt, i0, nchunks, kb, lane, bars, sin, sdel, dlo, dhi);
+  Pipe st{a, pitch, t0, nt, i0, nchunks, warp, lane, B, sin, sdel};
+  if (st.copies()) st.prologue();
 
   Tacc acc[DPW][SPL];
 #pragma unroll
@@ -181,26 +258,17 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
 #pragma unroll
     for (int q = 0; q < SPL; ++q) acc[m][q] = 0;
 
+  bool ok = true;
   for (int k = 0; k < nchunks; ++k) {
-    const uint32_t kg = kb + (uint32_t)k;
-    const int s = (int)(kg % STAGES);
-    const bool ok = mbar_wait_bounded(&bars[s], (kg / STAGES) & 1u, kWaitLimitCycles);
-    // The barrier also tells every thread that chunk k-1 is fully consumed.
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        report_error(a.status, kDevWaitTimeout);
-        // let copies already in flight land before the block moves on
-        for (int kk = k; kk < min(k + STAGES, nchunks); ++kk)
-          (void)mbar_wait_bounded(&bars[(kb + kk) % STAGES], ((kb + kk) / STAGES) & 1u, kWaitLimitCycles);
-      }
-      return false;
+    if (st.copies() && !st.ahead(k)) {
+      ok = false;
+      break;
     }
-    if (warp == 0 && k >= 1 && k - 1 + STAGES < nchunks) {
-      const int kn = k - 1 + STAGES, sn = (int)((kb + (uint32_t)kn) % STAGES);
-      stage_issue<Tin, BD, CC>(a, pitch, t0, nt, i0, kn, sn, lane, dlo, dhi, &bars[sn], sin, sdel);
-      stage_fetch<BD, CC>(a, i0, kn + 1, lane, dlo, dhi);
+    if (!stage_wait_full(B, k)) {
+      ok = false;
+      break;
     }
-
+    const int s = k % STAGES;
     const int c0 = k * CC;
     const int cn = min(CC, a.C - c0);
     for (int j = 0; j < cn; ++j) {
@@ -226,8 +294,13 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
         }
       }
     }
+    stage_release(B, k, lane);
   }
-  kbase = kb + (uint32_t)nchunks;
+  if (st.copies()) st.drain();
+  if (!ok) {
+    if (lane == 0) report_error(a.status, kDevWaitTimeout);
+    return;
+  }
 
   Tacc* __restrict__ out = static_cast<Tacc*>(a.out);
 #pragma unroll
@@ -241,15 +314,6 @@ __device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t
       }
     }
   }
-  return true;
-}
-
-template <typename Tin, bool WEIGHTED, int BD, int BT, int CC, int STAGES>
-__global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  init_stage_bars(reinterpret_cast<uint64_t*>(smem_raw), STAGES);
-  uint32_t kbase = 0;
-  (void)staged_tile<Tin, WEIGHTED, BD, BT, CC, STAGES>(a, pitch, blockIdx.x, blockIdx.y, kbase, smem_raw);
 }
 
 // ------------------------------------------------------------------- U8PK
@@ -268,8 +332,7 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
 // integer multiply-adds by a run-time 1 so that they issue to the FMA pipe,
 // leaving the ALU pipe to the byte permutes (two per word and channel).
 template <int WD, int WT, int DPW, int CC, int STAGES>
-__device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t bx, int by, uint32_t& kbase,
-                                          unsigned char* smem_raw) {
+__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int pitch) {
   constexpr int V = 16;
   constexpr int NW = WD * WT;
   constexpr int KW = 7;               // words per lane
@@ -278,22 +341,22 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
   constexpr int BT = 32 * SPL * WT;
   static_assert(BD % 4 == 0 && BT % 16 == 0, "tile shape");
   static_assert(kDmPad % BD == 0, "BD must divide the trial padding");
-  static_assert(STAGES * 8 <= kStBarBytes, "barrier area");
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  using Pipe = Stager<uint8_t, BD, CC, STAGES, NW, true>;
+  StageBars<STAGES>& B = init_stage_bars<STAGES>(smem_raw, NW, Pipe::kCopiers);
   uint8_t* sin = smem_raw + kStBarBytes;
   int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes + (size_t)STAGES * CC * pitch);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wd = warp % WD, wt = warp / WD;
-  const int64_t t0 = bx * BT;
-  const int i0 = by * BD;
+  const int64_t t0 = (int64_t)blockIdx.x * BT;
+  const int i0 = blockIdx.y * BD;
   const int nt = (int)min((int64_t)BT, a.n_out - t0);
   const int nchunks = (a.C + CC - 1) / CC;
-  const uint32_t kb = kbase;
 
-  int32_t dlo = 0, dhi = 0;  // warp 0: its lanes' delays of the next chunk to stage
-  if (warp == 0)
-    stage_prologue<uint8_t, BD, CC, STAGES>(a, pitch, t0, nt, i0, nchunks, kb, lane, bars, sin, sdel, dlo, dhi);
+  Pipe st{a, pitch, t0, nt, i0, nchunks, warp, lane, B, sin, sdel};
+  if (st.copies()) st.prologue();
 
   uint32_t ra[DPW][KW], rb[DPW][KW];  // A and B of each word (see above)
   int32_t tot[DPW][SPL];
@@ -344,23 +407,17 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
   };
 
   int since_flush = 0;
+  bool ok = true;
   for (int k = 0; k < nchunks; ++k) {
-    const uint32_t kg = kb + (uint32_t)k;
-    const int s = (int)(kg % STAGES);
-    const bool ok = mbar_wait_bounded(&bars[s], (kg / STAGES) & 1u, kWaitLimitCycles);
-    if (__syncthreads_or(!ok)) {
-      if (tid == 0) {
-        report_error(a.status, kDevWaitTimeout);
-        for (int kk = k; kk < min(k + STAGES, nchunks); ++kk)
-          (void)mbar_wait_bounded(&bars[(kb + kk) % STAGES], ((kb + kk) / STAGES) & 1u, kWaitLimitCycles);
-      }
-      return false;
+    if (st.copies() && !st.ahead(k)) {
+      ok = false;
+      break;
     }
-    if (warp == 0 && k >= 1 && k - 1 + STAGES < nchunks) {
-      const int kn = k - 1 + STAGES, sn = (int)((kb + (uint32_t)kn) % STAGES);
-      stage_issue<uint8_t, BD, CC>(a, pitch, t0, nt, i0, kn, sn, lane, dlo, dhi, &bars[sn], sin, sdel);
-      stage_fetch<BD, CC>(a, i0, kn + 1, lane, dlo, dhi);
+    if (!stage_wait_full(B, k)) {
+      ok = false;
+      break;
     }
+    const int s = k % STAGES;
     const int cn = min(CC, a.C - k * CC);
     int j = 0;
     for (; j + 1 < cn; j += 2) {
@@ -398,12 +455,16 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
       }
       since_flush += 1;
     }
+    stage_release(B, k, lane);
   }
   flush();
-  kbase = kb + (uint32_t)nchunks;
+  if (st.copies()) st.drain();
+  if (!ok && lane == 0) report_error(a.status, kDevWaitTimeout);
 
-  // transpose through shared memory (stage area is free: every chunk was consumed)
+  // transpose through shared memory (every warp is past the channel loop and
+  // no copy is in flight, so the stage area is free)
   __syncthreads();
+  if (!ok) return;
   int32_t* epi = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes) + (size_t)warp * DPW * 32 * SPL;
 #pragma unroll
   for (int m = 0; m < DPW; ++m)
@@ -419,15 +480,6 @@ __device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t b
     int32_t* orow = out + (int64_t)i * a.out_stride + t0 + tw0;
     for (int u = lane; u < lim; u += 32) orow[u] = epi[m * 32 * SPL + u];
   }
-  return true;
-}
-
-template <int WD, int WT, int DPW, int CC, int STAGES>
-__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int pitch) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  init_stage_bars(reinterpret_cast<uint64_t*>(smem_raw), STAGES);
-  uint32_t kbase = 0;
-  (void)u8pk_tile<WD, WT, DPW, CC, STAGES>(a, pitch, blockIdx.x, blockIdx.y, kbase, smem_raw);
 }
 
 __host__ __device__ constexpr int u8pk_smem_bytes(int stages, int cc, int bd, int pitch, int nw, int dpw) {
@@ -476,7 +528,8 @@ static cudaError_t launch_staged_t(const TileConfig& cfg, const FwdArgs& a, cuda
   X(4, 2, 2, 16, 4)      \
   X(8, 1, 4, 16, 3)      \
   X(4, 1, 2, 32, 3)      \
-  X(8, 2, 1, 16, 4)
+  X(8, 2, 1, 16, 4)      \
+  X(8, 1, 2, 32, 3)
 
 template <int WD, int WT, int DPW, int CC, int ST>
 static cudaError_t launch_u8pk_t(const TileConfig& cfg, const FwdArgs& a, cudaStream_t s) {

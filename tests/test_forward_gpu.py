@@ -168,3 +168,33 @@ def test_errors(dd):
     with pytest.raises(dd.DDError) as e:
         dd.Plan(0, 1400.0, 1.0, 1e-3, 0.0, 1.0, 4, 100)
     assert e.value.name == "DD_ERR_ARG"
+
+
+SATURATED = [
+    synth.Setup(f"sat-{c}", c, 1420.0, 300.0 / c, 50e-6, 0.0, 0.25, 12, 2100) for c in (255, 256, 257, 512, 513, 1024)
+]
+
+
+@pytest.mark.parametrize("setup", SATURATED, ids=lambda s: s.name)
+def test_u8_saturated_sums_are_exact(dd, setup):
+    """8-bit sums at their largest: every sample 255 gives exactly 255 * C at
+    every output (a closed form, no oracle), and random 0/255 samples match the
+    oracle bit for bit.  Channel counts straddle the 256-channel periods over
+    which the packed kernels' 16-bit partial sums are exact."""
+    c = setup.channels
+    d = oracle_table(setup)
+    for cfg in _all_configs(dd, setup, "u8"):
+        plan = dd.Plan.from_setup(setup, "u8")
+        plan.select(cfg)
+        stride = plan.padded_in_stride()
+        full = torch.full((c, stride), 255, dtype=torch.uint8, device="cuda")
+        out = plan.forward(full).cpu().numpy()
+        assert plan.device_status() == 0
+        assert (out == 255 * c).all(), f"{setup.name} {cfg}: saturated sum {out.min()}..{out.max()} != {255 * c}"
+        rng = np.random.default_rng(c)
+        x = np.zeros((c, stride), dtype=np.uint8)
+        x[:, :plan.n_in] = rng.choice(np.array([0, 255], dtype=np.uint8), size=(c, plan.n_in))
+        got = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert plan.device_status() == 0
+        ref, _ = oracle_window(d, x, "u8", 0, setup.n_dm, 0, setup.n_out)
+        assert_parity(got, ref, None, "u8", where=f"{setup.name} {cfg}")
