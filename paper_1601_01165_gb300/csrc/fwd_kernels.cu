@@ -388,22 +388,33 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
     asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(y), "r"(m), "r"(x));
     return d;
   };
-  // aligned words of (trial slot m, channel row j of stage s) -> x[KW]
-  auto aligned = [&](int s, int j, int m, uint32_t (&x)[KW]) {
-    const uint8_t* row = sin + (size_t)(s * CC + j) * pitch;
-    const int32_t* dl = sdel + (s * CC + j) * BD;
+  // The 4 bytes starting at byte (sel mod 4) of the 8 bytes lo, hi (lo first).
+  auto f4e = [](uint32_t lo, uint32_t hi, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32.f4e %0, %1, %2, %3;" : "=r"(d) : "r"(lo), "r"(hi), "r"(sel));
+    return d;
+  };
+  const int lane_off = wt * 32 * SPL + lane * SPL;  // this lane's first sample in the tile
+  // Channel row j of stage s: the row and the offset `cj` such that trial
+  // slot i's samples for this lane start at byte cj + dl[i] of the row (the
+  // row starts at t0 + dl[0] rounded down to 16 bytes; t0 is a multiple of 16).
+  auto channel = [&](int s, int j, const uint8_t*& row, const int32_t*& dl, int& cj) {
+    row = sin + (size_t)(s * CC + j) * pitch;
+    dl = sdel + (s * CC + j) * BD;
     const int d0 = dl[0];
-    const int64_t al = (t0 + d0) & ~(int64_t)(V - 1);
-    const int off = (int)(t0 + dl[wd * DPW + m] - al) + wt * 32 * SPL + lane * SPL;
-    const uint32_t* wp = reinterpret_cast<const uint32_t*>(row) + (off >> 2);
-    const uint32_t sel = 0x3210u + 0x1111u * (uint32_t)(off & 3);
+    cj = (int)(((uint32_t)t0 + (uint32_t)d0) & (uint32_t)(V - 1)) - d0 + lane_off;
+  };
+  // aligned words of trial slot m of a channel row -> x[KW]
+  auto aligned = [&](const uint8_t* row, const int32_t* dl, int cj, int m, uint32_t (&x)[KW]) {
+    const int off = cj + dl[wd * DPW + m];
+    const uint32_t* wp = reinterpret_cast<const uint32_t*>(row + (off & ~3));
     uint32_t wv[KW + 1];
     // the KW + 1 words stay inside the channel's shared-memory row
     if (!DD_INDEX_OK(a.status, off >= 0 && (off >> 2) + KW + 1 <= pitch / 4)) wp = reinterpret_cast<const uint32_t*>(row);
 #pragma unroll
     for (int w = 0; w <= KW; ++w) wv[w] = wp[w];
 #pragma unroll
-    for (int w = 0; w < KW; ++w) x[w] = __byte_perm(wv[w], wv[w + 1], sel);
+    for (int w = 0; w < KW; ++w) x[w] = f4e(wv[w], wv[w + 1], (uint32_t)off);
   };
 
   int since_flush = 0;
@@ -425,11 +436,16 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
         flush();
         since_flush = 0;
       }
+      const uint8_t *row0, *row1;
+      const int32_t *dl0, *dl1;
+      int c0j, c1j;
+      channel(s, j, row0, dl0, c0j);
+      channel(s, j + 1, row1, dl1, c1j);
 #pragma unroll
       for (int m = 0; m < DPW; ++m) {
         uint32_t x0[KW], x1[KW];
-        aligned(s, j, m, x0);
-        aligned(s, j + 1, m, x1);
+        aligned(row0, dl0, c0j, m, x0);
+        aligned(row1, dl1, c1j, m, x1);
 #pragma unroll
         for (int w = 0; w < KW; ++w) {
           ra[m][w] = madd(madd(ra[m][w], x0[w], one), x1[w], one);
@@ -443,10 +459,14 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
         flush();
         since_flush = 0;
       }
+      const uint8_t* row0;
+      const int32_t* dl0;
+      int c0j;
+      channel(s, j, row0, dl0, c0j);
 #pragma unroll
       for (int m = 0; m < DPW; ++m) {
         uint32_t x0[KW];
-        aligned(s, j, m, x0);
+        aligned(row0, dl0, c0j, m, x0);
 #pragma unroll
         for (int w = 0; w < KW; ++w) {
           ra[m][w] = madd(ra[m][w], x0[w], one);
