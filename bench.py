@@ -43,12 +43,13 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ_NOMINAL = 2070.0
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
-# keyed by (kernel config, dtype); valid only while the kernel source hash matches.
+# keyed by (setup name, output samples, kernel config, dtype); valid only while
+# the kernel source hash matches.
 NCU_TRAFFIC = {
-    # profiles/fwd_tmw6_f32_apertif.md: 113.0 MB read + 128.2 MB written
-    ("tmw6_f32_d6_t4096", "f32"): {"bytes": 241_261_568, "hash": "0d02045a17aa9c28"},
-    # profiles/fwd_u8pk_u8_apertif.md: 32.4 MB read + 113.0 MB written
-    ("u8pk_w8x1_d2_c16_st4", "u8"): {"bytes": 145_410_048, "hash": "0d02045a17aa9c28"},
+    # profiles/fwd_tmw6_f32_apertif.md: 113.3 MB read + 128.5 MB written
+    ("apertif", 20000, "tmw6_f32_d6_t4096", "f32"): {"bytes": 241_816_576, "hash": "a9a29efb7292cfbd"},
+    # profiles/fwd_u8pk_u8_apertif.md: 32.6 MB read + 111.8 MB written
+    ("apertif", 20000, "u8pk_w8x1_d2_c32_st3", "u8"): {"bytes": 144_425_728, "hash": "a9a29efb7292cfbd"},
 }
 
 
@@ -391,7 +392,7 @@ def run_ours(args, setup):
     achieved_alu = adds / (avg_ms / 1e3) / 1e12
     achieved_hbm = compulsory / (avg_ms / 1e3) / 1e9
     kh = _kernel_hash()
-    tr = NCU_TRAFFIC.get((cfg_name, args.dtype))
+    tr = NCU_TRAFFIC.get((setup.name, setup.n_out, cfg_name, args.dtype))
     traffic = tr["bytes"] if tr and tr.get("hash") == kh else None
     roof = {"bound": "alu", "achieved": achieved_alu, "peak": add_peak,
             "unit": "TFLOP/s" if args.dtype == "f32" else "Tops", "frac": achieved_alu / add_peak,
