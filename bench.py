@@ -401,7 +401,12 @@ def run_ours(args, setup):
                          f"1 add = 1 op (Eq. 2 counts one add per input sample)",
             "per_launch_ops": adds, "avg_launch_ms": avg_ms,
             "hbm": {"achieved_gbs": achieved_hbm, "peak_gbs": hbm_gbs, "frac": achieved_hbm / hbm_gbs,
-                    "compulsory_bytes": compulsory, "peak_kind": peak_kind}}
+                    "compulsory_bytes": compulsory, "peak_kind": peak_kind,
+                    "ncu_traffic_gbs": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9,
+                    "ncu_traffic_frac": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9 / hbm_gbs},
+            # Eq. 2's accounting: every add reads its own 4-byte sample (no reuse); an
+            # effective rate for comparison with the paper's figures, not bytes moved
+            "eq2_effective_gbs": 4.0 * adds / (avg_ms / 1e3) / 1e9}
     clocks = sampler.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -61,6 +61,10 @@ RAGGED = [
     synth.Setup("zero-dm", 64, 1400.0, 1.0, 1e-3, 0.0, 0.0, 2, 1500),
     synth.Setup("lofar-cut", 32, 138.0, 0.1953125, 5e-6, 0.0, 0.01, 70, 3001),
     synth.Setup("apertif-cut", 1024, 1420.0, 0.29296875, 50e-6, 3.0, 0.25, 41, 1931),
+    # one channel: a single chunk in which most copying lanes have nothing to copy
+    synth.Setup("one-channel", 1, 1420.0, 1.0, 50e-6, 0.0, 0.25, 7, 1777),
+    # a 32-channel chunk and a 1-channel chunk; 70 trials end inside a DM block
+    synth.Setup("c33", 33, 1420.0, 300.0 / 33, 50e-6, 0.0, 0.25, 70, 2500),
 ]
 
 
