@@ -233,7 +233,7 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
   constexpr int NW = 8;
   constexpr int DPW = BD / NW;
   constexpr int SPL = BT / 32;
-  static_assert(BD % NW == 0 && BT % 32 == 0 && BD % 4 == 0, "tile shape");
+  static_assert(BD % NW == 0 && BT % 64 == 0 && BD % 4 == 0, "tile shape (an even number of samples per lane)");
   // a block's delay slice [i0, i0 + BD) must stay inside the padded row
   static_assert(kDmPad % BD == 0, "BD must divide the trial padding");
 
@@ -283,14 +283,19 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
 #pragma unroll
       for (int m = 0; m < DPW; ++m) {
         const int off = base + dl[warp + m * NW] - d0 + lane;
+        if constexpr (sizeof(Tin) == 4) {
+          // float: packed pairs of adds (same results, half the add instructions)
 #pragma unroll
-        for (int q = 0; q < SPL; ++q) {
-          const Tin v = row[off + 32 * q];
-          if constexpr (WEIGHTED) {
-            acc[m][q] = fmaf(wc, v, acc[m][q]);
-          } else {
-            acc[m][q] += (Tacc)v;
+          for (int q = 0; q < SPL; q += 2) {
+            if constexpr (WEIGHTED) {
+              fma2_rn(acc[m][q], acc[m][q + 1], wc, row[off + 32 * q], row[off + 32 * q + 32]);
+            } else {
+              add2_rn(acc[m][q], acc[m][q + 1], row[off + 32 * q], row[off + 32 * q + 32]);
+            }
           }
+        } else {
+#pragma unroll
+          for (int q = 0; q < SPL; ++q) acc[m][q] += (Tacc)row[off + 32 * q];
         }
       }
     }

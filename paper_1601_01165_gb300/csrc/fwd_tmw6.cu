@@ -254,18 +254,19 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
         if (cn < C) ok = write_window(cn, (kLead - set) + p);
       }
       tmem_wait_ld();
+      // packed pairs: half the add instructions of scalar code, same results
       if constexpr (WEIGHTED) {
         const float wc = __int_as_float(si.z);
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          acc[0][u] = fmaf(wc, v0[u], acc[0][u]);
-          acc[1][u] = fmaf(wc, v1[u], acc[1][u]);
+        for (int u = 0; u < 32; u += 2) {
+          fma2_rn(acc[0][u], acc[0][u + 1], wc, v0[u], v0[u + 1]);
+          fma2_rn(acc[1][u], acc[1][u + 1], wc, v1[u], v1[u + 1]);
         }
       } else {
 #pragma unroll
-        for (int u = 0; u < 32; ++u) {
-          acc[0][u] += v0[u];
-          acc[1][u] += v1[u];
+        for (int u = 0; u < 32; u += 2) {
+          add2_rn(acc[0][u], acc[0][u + 1], v0[u], v0[u + 1]);
+          add2_rn(acc[1][u], acc[1][u + 1], v1[u], v1[u + 1]);
         }
       }
     }

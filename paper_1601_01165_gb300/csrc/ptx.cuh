@@ -122,6 +122,24 @@ __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Each thread loads 32 consecutive 32-bit columns of its own lane.
+// Two independent fp32 additions, a_k + b_k rounded to nearest, in one
+// instruction; each lane's result is the scalar add's bit for bit.
+__device__ __forceinline__ void add2_rn(float& a0, float& a1, float b0, float b1) {
+  asm("{\n .reg .b64 x, y;\n mov.b64 x, {%0, %1};\n mov.b64 y, {%2, %3};\n add.rn.f32x2 x, x, y;\n"
+      " mov.b64 {%0, %1}, x;\n}\n"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b0), "f"(b1));
+}
+
+// Two independent fused multiply-adds, w * b_k + a_k with one rounding each,
+// in one instruction; each lane's result is fmaf's bit for bit.
+__device__ __forceinline__ void fma2_rn(float& a0, float& a1, float w, float b0, float b1) {
+  asm("{\n .reg .b64 x, y, s;\n mov.b64 x, {%0, %1};\n mov.b64 y, {%2, %3};\n mov.b64 s, {%4, %4};\n"
+      " fma.rn.f32x2 x, s, y, x;\n mov.b64 {%0, %1}, x;\n}\n"
+      : "+f"(a0), "+f"(a1)
+      : "f"(b0), "f"(b1), "f"(w));
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
