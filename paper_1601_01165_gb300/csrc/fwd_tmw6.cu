@@ -65,8 +65,8 @@ static_assert(kTileBytes + 16 <= kStage, "stage holds tile and descriptor");
 static_assert(kT * kBT * 4 <= kNStages * kStage, "output tile fits the stage area");
 
 struct Hdr {
-  uint64_t sfull[12][kWS];   // per warp: its stages
-  int4 slot[4][2 * kLead];   // per quadrant window slot: column bytes (2 words), weight bits
+  uint64_t sfull[12][kWS];           // per warp: its stages
+  uint4 slot[4][2 * kLead][kLead];   // per quadrant window slot and reading warp: its 2 trials' TMEM addresses, weight bits
   uint32_t tbase;
   int failed;
 };
@@ -77,24 +77,19 @@ static_assert(sizeof(Hdr) <= kHdr, "header fits");
 // which is rbase(y) ^ (x << 4) with rbase(y) = y * 128 + ((y & 7) << 4).
 __device__ __forceinline__ uint32_t rbase(int y) { return (uint32_t)y * 128u + ((uint32_t)(y & 7) << 4); }
 
-// Four consecutive chunks of one row (compile-time chunk index X0..X0+3).
-template <int X0>
-__device__ __forceinline__ void ld_group(const unsigned char* tile, uint32_t rb, float* v) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const float4 x = *reinterpret_cast<const float4*>(tile + (rb ^ (uint32_t)((X0 + k) << 4)));
-    v[4 * k] = x.x, v[4 * k + 1] = x.y, v[4 * k + 2] = x.z, v[4 * k + 3] = x.w;
-  }
+// One 16-byte chunk of each lane's row to 4 TMEM columns.
+__device__ __forceinline__ void st4(uint32_t taddr, float4 x) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "f"(x.x), "f"(x.y),
+               "f"(x.z), "f"(x.w));
 }
 
-// TMEM stores that read registers only: ordered with the other tcgen05
-// instructions (volatile), not with shared-memory accesses.
-__device__ __forceinline__ void st16_regs(uint32_t taddr, const float* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "f"(v[0]), "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7]), "f"(v[8]), "f"(v[9]),
-      "f"(v[10]), "f"(v[11]), "f"(v[12]), "f"(v[13]), "f"(v[14]), "f"(v[15]));
+// Four consecutive chunks of one row (compile-time chunk index X0..X0+3),
+// each stored to TMEM as it arrives.
+template <int X0>
+__device__ __forceinline__ void copy_group(const unsigned char* tile, uint32_t rb, uint32_t taddr) {
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    st4(taddr + 4 * k, *reinterpret_cast<const float4*>(tile + (rb ^ (uint32_t)((X0 + k) << 4))));
 }
 
 }  // namespace
@@ -128,6 +123,14 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
   __syncthreads();
   tmem_fence_after_sync();
   const uint32_t tq = H.tbase + ((uint32_t)(32 * q) << 16);  // this quadrant's lanes, column 0
+  // slots start with in-range addresses (column 0 of the slot) and unit weight,
+  // so a window left unwritten after a timeout is never read out of range
+  if (lane == 0)
+    for (int sl = p; sl < 2 * kLead; sl += kLead)
+      for (int pr = 0; pr < kLead; ++pr) {
+        const uint32_t c0 = tq + (uint32_t)(kSlot * sl);
+        H.slot[q][sl][pr] = make_uint4(c0, c0, __float_as_uint(1.0f), 0u);
+      }
 
   // ------------------------------------------------ this warp's tile loads
   // Warp (q, p) writes the windows of channels c = p (mod 3) for quadrant q.
@@ -176,30 +179,39 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
     const int need = dsc.w;  // floats from the aligned start: shift + 32 + max offset
     const int lead = 4 * (c4 & 3);
     const int ng = (lead + need + 15) >> 4;  // 3..5
+    const uint32_t col = tq + (uint32_t)(kSlot * sl);
     // the window's groups stay inside the slot and the tile's rows
     if (!DD_INDEX_OK(a.status, need >= 32 && lead + need <= kSlot && lane + 2 < kQRows)) return true;
-    const uint32_t col = tq + (uint32_t)(kSlot * sl);
     const uint32_t rb0 = rbase(lane), rb1 = rbase(lane + 1), rb2 = rbase(lane + 2);
-    float v[16];
     if (c4 < 4) {  // groups 0..4: row lane (0, 1), row lane + 1 (2, 3), row lane + 2 (4)
-      ld_group<0>(st, rb0, v), st16_regs(col, v);
-      ld_group<4>(st, rb0, v), st16_regs(col + 16, v);
-      ld_group<0>(st, rb1, v), st16_regs(col + 32, v);
-      if (ng > 3) ld_group<4>(st, rb1, v), st16_regs(col + 48, v);
-      if (ng > 4) ld_group<0>(st, rb2, v), st16_regs(col + 64, v);
+      copy_group<0>(st, rb0, col);
+      copy_group<4>(st, rb0, col + 16);
+      copy_group<0>(st, rb1, col + 32);
+      if (ng > 3) copy_group<4>(st, rb1, col + 48);
+      if (ng > 4) copy_group<0>(st, rb2, col + 64);
     } else {  // groups 1..5
-      ld_group<4>(st, rb0, v), st16_regs(col, v);
-      ld_group<0>(st, rb1, v), st16_regs(col + 16, v);
-      ld_group<4>(st, rb1, v), st16_regs(col + 32, v);
-      if (ng > 3) ld_group<0>(st, rb2, v), st16_regs(col + 48, v);
-      if (ng > 4) ld_group<4>(st, rb2, v), st16_regs(col + 64, v);
+      copy_group<4>(st, rb0, col);
+      copy_group<0>(st, rb1, col + 16);
+      copy_group<4>(st, rb1, col + 32);
+      if (ng > 3) copy_group<0>(st, rb2, col + 48);
+      if (ng > 4) copy_group<4>(st, rb2, col + 64);
     }
     float wc = 1.0f;
     if constexpr (WEIGHTED) wc = __ldg(a.w + c);
     __syncwarp();
     if (lane == 0) {
-      // column bytes of the 6 trials, moved by the window's lead (bytes stay < 256)
-      H.slot[q][sl] = make_int4(dsc.y + lead * 0x01010101, dsc.z + lead * 0x0101, __float_as_int(wc), 0);
+      // each trial's TMEM address: the slot's column, the window's lead and the
+      // trial's column byte; its 32 columns stay inside the slot
+      uint32_t ta[kT];
+#pragma unroll
+      for (int jt = 0; jt < kT; ++jt) {
+        uint32_t b = (uint32_t)lead + (((uint32_t)(jt < 4 ? dsc.y : dsc.z) >> (8 * (jt & 3))) & 0xffu);
+        if (!DD_INDEX_OK(a.status, b + 32 <= (uint32_t)kSlot)) b = 0;
+        ta[jt] = col + b;
+      }
+#pragma unroll
+      for (int pr = 0; pr < kLead; ++pr)
+        H.slot[q][sl][pr] = make_uint4(ta[2 * pr], ta[2 * pr + 1], __float_as_uint(wc), 0u);
       // the stage is read: reload it with this warp's channel kAhead later
       // (the window's shared loads have completed: the TMEM stores consumed them)
       if (c + kAhead < C) {
@@ -231,7 +243,6 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
   for (int jj = 0; jj < 2; ++jj)
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[jj][k] = 0.0f;
-  const int shift_a = 16 * (p & 1), word_a = p >> 1;  // where trial 2p's column byte sits
   const int n_steps = (C + kLead - 1) / kLead;
   for (int n = 0; n < n_steps; ++n) {
     const int set = (n & 1) * kLead;  // slots of this step's windows
@@ -239,15 +250,10 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
     for (int k = 0; k < kLead; ++k) {
       const int c = kLead * n + k;
       if (c >= C) break;  // the same for every warp
-      const int4 si = H.slot[q][set + k];
-      const uint32_t bytes = (uint32_t)(word_a ? si.y : si.x) >> shift_a;
-      const uint32_t col = tq + (uint32_t)(kSlot * (set + k));
-      // both trials' 32 columns stay inside the slot (warp-uniform)
-      if (!DD_INDEX_OK(a.status, (bytes & 0xffu) + 32 <= (uint32_t)kSlot && ((bytes >> 8) & 0xffu) + 32 <= (uint32_t)kSlot))
-        continue;
+      const uint4 ta = H.slot[q][set + k][p];  // trials 2p, 2p + 1 and the channel's weight
       float v0[32], v1[32];
-      tmem_ld32(col + (bytes & 0xffu), v0);
-      tmem_ld32(col + ((bytes >> 8) & 0xffu), v1);
+      tmem_ld32(ta.x, v0);
+      tmem_ld32(ta.y, v1);
       // while the step's last loads are in flight: this warp's window of the next step
       if (k == kLead - 1 && ok) {
         const int cn = kLead * (n + 1) + p;
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
       tmem_wait_ld();
       // packed pairs: half the add instructions of scalar code, same results
       if constexpr (WEIGHTED) {
-        const float wc = __int_as_float(si.z);
+        const float wc = __uint_as_float(ta.z);
 #pragma unroll
         for (int u = 0; u < 32; u += 2) {
           fma2_rn(acc[0][u], acc[0][u + 1], wc, v0[u], v0[u + 1]);
