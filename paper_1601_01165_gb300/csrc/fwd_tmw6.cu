@@ -198,20 +198,17 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
     }
     float wc = 1.0f;
     if constexpr (WEIGHTED) wc = __ldg(a.w + c);
+    // lane pr < 3 publishes reading warp pr's entry: its trials' TMEM addresses
+    // (the slot's column, the window's lead and the trial's column byte; the 32
+    // columns stay inside the slot) and the channel's weight
+    if (lane < kLead) {
+      const uint32_t bytes = (uint32_t)(lane < 2 ? dsc.y : dsc.z) >> (16 * (lane & 1));
+      uint32_t b0 = (uint32_t)lead + (bytes & 0xffu), b1 = (uint32_t)lead + ((bytes >> 8) & 0xffu);
+      if (!DD_INDEX_OK(a.status, b0 + 32 <= (uint32_t)kSlot && b1 + 32 <= (uint32_t)kSlot)) b0 = b1 = 0;
+      H.slot[q][sl][lane] = make_uint4(col + b0, col + b1, __float_as_uint(wc), 0u);
+    }
     __syncwarp();
     if (lane == 0) {
-      // each trial's TMEM address: the slot's column, the window's lead and the
-      // trial's column byte; its 32 columns stay inside the slot
-      uint32_t ta[kT];
-#pragma unroll
-      for (int jt = 0; jt < kT; ++jt) {
-        uint32_t b = (uint32_t)lead + (((uint32_t)(jt < 4 ? dsc.y : dsc.z) >> (8 * (jt & 3))) & 0xffu);
-        if (!DD_INDEX_OK(a.status, b + 32 <= (uint32_t)kSlot)) b = 0;
-        ta[jt] = col + b;
-      }
-#pragma unroll
-      for (int pr = 0; pr < kLead; ++pr)
-        H.slot[q][sl][pr] = make_uint4(ta[2 * pr], ta[2 * pr + 1], __float_as_uint(wc), 0u);
       // the stage is read: reload it with this warp's channel kAhead later
       // (the window's shared loads have completed: the TMEM stores consumed them)
       if (c + kAhead < C) {
@@ -244,6 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_cons
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[jj][k] = 0.0f;
   const int n_steps = (C + kLead - 1) / kLead;
+#pragma unroll 2
   for (int n = 0; n < n_steps; ++n) {
     const int set = (n & 1) * kLead;  // slots of this step's windows
 #pragma unroll
