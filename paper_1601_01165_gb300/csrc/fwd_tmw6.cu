@@ -13,17 +13,20 @@
 //    hold the current step's windows and the next step's.
 //  * 12 warps, 3 per TMEM lane quadrant (warp w serves lanes 32 (w % 4) ..,
 //    which is also its SM sub-partition); warp p = w / 4 owns trials 2p and
-//    2p + 1.  Each channel it issues two 32-column loads at column shift + o_j
-//    (o_j = delay(c, i0 + j) - delay(c, i0)) and waits once; 64 adds follow.
+//    2p + 1.  Each channel it reads its slot entry (its two trials' TMEM
+//    addresses: the slot's column plus shift + o_j, o_j = delay(c, i0 + j) -
+//    delay(c, i0), and the channel weight), issues two 32-column loads and
+//    waits once; 32 packed adds (two IEEE adds per instruction) follow.
 //  * Warp p of a quadrant writes the quadrant's window of channel p of the
 //    next step of three channels, while its TMEM loads of the step's last
 //    channel are in flight.  The input comes from its private stages: a 3-D
 //    TMA load (128-byte swizzle) of the quadrant's 35 rows of 32 samples from
 //    the row holding t0 + delay(c, i0), plus the channel's 16-byte descriptor
 //    (base delay, column bytes, window width); 16-byte shared loads read the
-//    swizzled rows without bank conflicts.  Once a window is out, the warp
-//    reloads the stage with its channel nine later, so quadrants never wait
-//    on each other.
+//    swizzled rows without bank conflicts, each going straight to 4 TMEM
+//    columns.  Three lanes then publish the reading warps' slot entries.
+//    Once a window is out, the warp reloads the stage with its channel nine
+//    later, so quadrants never wait on each other.
 //  * The quadrant's three warps meet at a named barrier after each step: the
 //    next step's windows are then in TMEM and this step's slots are free.
 //
