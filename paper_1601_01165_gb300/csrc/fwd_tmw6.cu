@@ -101,8 +101,10 @@ template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads, 1) fwd_tmw6_kernel(const __grid_constant__ CUtensorMap tmap, FwdArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   Hdr& H = *reinterpret_cast<Hdr*>(smem_raw);
-  unsigned char* stages = reinterpret_cast<unsigned char*>(
-      (reinterpret_cast<uintptr_t>(smem_raw) + kHdr + 1023) & ~static_cast<uintptr_t>(1023));
+  // stages on the first 1024-byte boundary (of the shared address) past the
+  // header; indexing the shared array keeps every access a shared one
+  const uint32_t sbase = smem_u32(smem_raw);
+  unsigned char* stages = smem_raw + (((sbase + kHdr + 1023u) & ~1023u) - sbase);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int q = warp & 3, p = warp >> 2;
