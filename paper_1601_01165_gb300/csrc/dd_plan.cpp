@@ -118,9 +118,9 @@ void free_plan_device(dd_plan_s* p) {
 }
 
 // Default configuration: the first valid entry of a preference list, in
-// the order measured on the Table 2 setups (Apertif float: TMW6 4.84 ms,
-// staged d8/t1024 4.94 ms; LOFAR float: staged d8/t1024 3.19 ms, d32/t512/c8
-// 3.13 ms; Apertif uint8: U8PK c32 2.70 ms); dd_tune replaces it with a
+// the order measured on the Table 2 setups (Apertif float: TMW6 4.07 ms,
+// staged d8/t1024 4.94 ms; LOFAR float: staged d8/t1024 3.16 ms, d32/t384
+// 3.12 ms; Apertif uint8: U8PK c32 2.22 ms); dd_tune replaces it with a
 // measured choice.  TMW6 is offered only where a 6-trial group's offsets fit
 // its windows (Apertif, not LOFAR).
 static const char* const kPrefsF32[] = {"tmw6_f32_d6_t4096",     "staged_d8_t1024_c4_s3", "staged_d16_t512_c8_s3",
