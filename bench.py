@@ -430,7 +430,7 @@ def run_ours(args, setup):
 
 
 def run_batched(args):
-    """64 uneven beams: one persistent launch (CUDA graph) vs 64 plain launches of the same plans."""
+    """64 uneven beams: one CUDA-graph launch of every beam's forward vs 64 plain launches of the same plans."""
     import torch
     from paper_1601_01165_gb300 import binding as dd
     torch.cuda.set_device(0)
@@ -488,6 +488,81 @@ def run_batched(args):
                                    f"10k-200k samples, Apertif/LOFAR grids, mixed uint8/float32), seed {args.seed}"}}
     print(json.dumps(line), flush=True)
     return 0 if same else 1
+
+
+def run_autograd(args):
+    """The differentiable configuration: learnable per-channel weights on the
+    Apertif-like float beam, dedispersion -> 8-sample boxcar -> -max S/N loss,
+    backward to the weights (the adjoint of Algorithm 1 and the per-channel
+    dot products).  One step = forward + loss + backward; the value counts
+    the forward's DM-trial samples per second of whole steps."""
+    import torch
+    from paper_1601_01165_gb300 import binding as dd
+    from paper_1601_01165_gb300.autograd import boxcar_snr_loss, dedisperse
+    torch.cuda.set_device(0)
+    setup = synth.APERTIF
+    plan = dd.Plan.from_setup(setup, "f32")
+    g = torch.Generator(device="cuda").manual_seed(args.seed)
+    in_bytes = setup.channels * plan.padded_in_stride() * 4
+    n_buf = max(2, -(-2 * L2_BYTES // in_bytes) + 1)
+    xs = []
+    for _ in range(n_buf):
+        x = plan.alloc_input()
+        x.normal_(generator=g)
+        xs.append(x)
+    w = torch.ones(setup.channels, device="cuda", requires_grad=True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    parts = [0.0, 0.0, 0.0]
+    loss_val = None
+
+    def step(k, timed):
+        nonlocal loss_val
+        w.grad = None
+        if timed:
+            ev[0].record()
+        out = dedisperse(xs[k % n_buf], w, plan)
+        if timed:
+            ev[1].record()
+        loss = boxcar_snr_loss(out)
+        if timed:
+            ev[2].record()
+        loss.backward()
+        if timed:
+            ev[3].record()
+            torch.cuda.synchronize()
+            for j in range(3):
+                parts[j] += ev[j].elapsed_time(ev[j + 1])
+        loss_val = loss
+
+    for k in range(args.warmup):
+        step(k, False)
+    torch.cuda.synchronize()
+    # whole steps back to back (no synchronisation inside the timed region)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(args.steps):
+        step(k, False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    # the parts, each step synchronised (reported beside the back-to-back time)
+    kp = min(args.steps, 10)
+    for k in range(kp):
+        step(k, True)
+    if plan.device_status() != 0:
+        raise RuntimeError("device status nonzero after timed region")
+    gw = w.grad
+    line = {"metric": METRIC, "workload": "autograd", "value": setup.n_dm * setup.n_out / (ms / 1e3), "unit": UNIT,
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "forward_ms": parts[0] / kp, "loss_ms": parts[1] / kp, "backward_ms": parts[2] / kp,
+            "loss": float(loss_val.item()), "grad_w_finite": bool(torch.isfinite(gw).all().item()),
+            "config": {"workload": f"apertif-like beam ({setup.channels} ch, {setup.n_dm} DM trials, {setup.n_out} "
+                                   f"samples, float32), learnable channel weights, 8-sample boxcar -max S/N loss, "
+                                   f"backward to the weights; {n_buf} rotating inputs > 2x L2",
+                       "kernel_config": plan.selected}}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_dm_sweep(args):
@@ -578,7 +653,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--dtype", choices=["f32", "u8"], default="f32")
     ap.add_argument("--config", default=None, help="kernel configuration name (default: plan's choice)")
-    ap.add_argument("--workload", choices=["apertif", "lofar", "batched", "serving", "dm-sweep"], default="apertif")
+    ap.add_argument("--workload", choices=["apertif", "lofar", "batched", "serving", "dm-sweep", "autograd"],
+                    default="apertif")
     ap.add_argument("--beams", type=int, default=None, help="batched: 64, serving: 40")
     ap.add_argument("--chunks", type=int, default=4, help="serving: chunks per beam")
     ap.add_argument("--budget-gb", type=float, default=None, help="serving: HBM budget")
@@ -598,6 +674,8 @@ def main():
         return run_serving(args)
     if args.workload == "dm-sweep":
         return run_dm_sweep(args)
+    if args.workload == "autograd":
+        return run_autograd(args)
     setup = synth.APERTIF if args.workload == "apertif" else synth.LOFAR
     if args.n_out:
         setup = setup.replace(n_out=args.n_out)

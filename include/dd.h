@@ -82,6 +82,20 @@ dd_status dd_plan(dd_plan_t* out, int32_t channels, double f_low_mhz, double cha
                   int64_t n_out, dd_dtype dtype);
 
 /*
+ * A plan over DM trials [dm_index0, dm_index0 + n_dm) of the grid
+ * DM_i = dm_first + i * dm_step: trial j of the plan has DM_(dm_index0 + j),
+ * computed exactly as dd_plan computes it, so its delay rows and outputs equal
+ * rows dm_index0 .. dm_index0 + n_dm - 1 of the full plan's bit for bit.
+ * Beams are split across GPUs this way (Section 2: every DM trial is an
+ * independent sum): each GPU reads the whole input and writes its own rows;
+ * nothing is reduced.  dm_index0 >= 0 and dm_index0 + n_dm < 2^31; otherwise
+ * as dd_plan (dd_plan is dm_index0 = 0).
+ */
+dd_status dd_plan_dm_range(dd_plan_t* out, int32_t channels, double f_low_mhz, double chan_bw_mhz,
+                           double t_samp_s, double dm_first, double dm_step, int32_t dm_index0, int32_t n_dm,
+                           int64_t n_out, dd_dtype dtype);
+
+/*
  * Host-only: the delay table of Eq. 1 exactly as dd_plan computes it, written
  * to `host_out` ([n_dm][channels] int32, row-major) without touching a GPU.
  * Same argument rules and errors as dd_plan (DD_ERR_ARG).

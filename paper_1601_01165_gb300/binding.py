@@ -64,6 +64,7 @@ def _declare(lib):
     P32, P64, PD = ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(dbl)
     sig = {
         "dd_plan": (st, [ctypes.POINTER(vp), i32, dbl, dbl, dbl, dbl, dbl, i32, i64, st]),
+        "dd_plan_dm_range": (st, [ctypes.POINTER(vp), i32, dbl, dbl, dbl, dbl, dbl, i32, i32, i64, st]),
         "dd_delay_table": (st, [i32, dbl, dbl, dbl, dbl, dbl, i32, vp]),
         "dd_plan_destroy": (st, [vp]),
         "dd_plan_info": (st, [vp, P64, P32, P64]),
@@ -145,13 +146,14 @@ class Plan:
     """
 
     def __init__(self, channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm, n_out,
-                 dtype: str = "f32"):
+                 dtype: str = "f32", dm_index0: int = 0):
         lib = load()
         h = ctypes.c_void_p()
-        check(lib.dd_plan(ctypes.byref(h), channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step,
-                          n_dm, n_out, _DTYPES[dtype]), "dd_plan")
+        check(lib.dd_plan_dm_range(ctypes.byref(h), channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step,
+                                   dm_index0, n_dm, n_out, _DTYPES[dtype]), "dd_plan_dm_range")
         self._h = h
         self.channels, self.n_dm, self.n_out, self.dtype = channels, n_dm, n_out, dtype
+        self.dm_index0 = dm_index0
         self.geometry = (channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm, n_out)
         n_in, md, db = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64()
         check(lib.dd_plan_info(h, ctypes.byref(n_in), ctypes.byref(md), ctypes.byref(db)), "dd_plan_info")
@@ -162,6 +164,14 @@ class Plan:
     @classmethod
     def from_setup(cls, setup, dtype="f32"):
         return cls(*setup.plan_args(), dtype=dtype)
+
+    @classmethod
+    def dm_range(cls, setup, i0, i1, dtype="f32"):
+        """The plan of trials [i0, i1) of the setup's DM grid: its outputs are
+        rows i0 .. i1 - 1 of the full plan's, bit for bit (dd_plan_dm_range)."""
+        args = list(setup.plan_args())
+        args[6] = i1 - i0  # n_dm
+        return cls(*args, dtype=dtype, dm_index0=i0)
 
     @property
     def handle(self):

@@ -96,6 +96,7 @@ struct dd_plan_s {
   int64_t n_out = 0, n_in = 0;
   int32_t max_delay = 0;
   double f_low = 0, chan_bw = 0, t_samp = 0, dm_first = 0, dm_step = 0;
+  int32_t dm_index0 = 0;              // trial i of the plan is trial dm_index0 + i of the DM grid
   dd_dtype dtype = DD_F32_F32;
   std::vector<int32_t> delays;        // host copy [n_dm][C]
   int32_t* d_delays = nullptr;        // [n_dm][C]

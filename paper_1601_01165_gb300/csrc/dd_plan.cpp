@@ -29,7 +29,7 @@ static dd_status compute_delay_table(dd_plan_s& p) {
   const double inv_fh2 = 1.0 / (f_h * f_h);
   p.delays.assign((size_t)p.n_dm * p.C, 0);
   for (int32_t i = 0; i < p.n_dm; ++i) {
-    const double kdm = 4150.0 * (p.dm_first + (double)i * p.dm_step);
+    const double kdm = 4150.0 * (p.dm_first + (double)(p.dm_index0 + i) * p.dm_step);
     for (int32_t c = 0; c < p.C; ++c) {
       const double f = p.f_low + (double)c * p.chan_bw;
       const double samples = kdm * (1.0 / (f * f) - inv_fh2) / p.t_samp;
@@ -267,10 +267,18 @@ extern "C" dd_status dd_delay_table(int32_t channels, double f_low_mhz, double c
 extern "C" dd_status dd_plan(dd_plan_t* out, int32_t channels, double f_low_mhz, double chan_bw_mhz,
                              double t_samp_s, double dm_first, double dm_step, int32_t n_dm, int64_t n_out,
                              dd_dtype dtype) {
+  return dd_plan_dm_range(out, channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, 0, n_dm, n_out, dtype);
+}
+
+extern "C" dd_status dd_plan_dm_range(dd_plan_t* out, int32_t channels, double f_low_mhz, double chan_bw_mhz,
+                                      double t_samp_s, double dm_first, double dm_step, int32_t dm_index0,
+                                      int32_t n_dm, int64_t n_out, dd_dtype dtype) {
   clear_error();
   if (!out) return set_error(DD_ERR_ARG, "dd_plan: out is NULL");
   dd_status chk = check_plan_args(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm);
   if (chk != DD_OK) return chk;
+  if (dm_index0 < 0 || (int64_t)dm_index0 + n_dm > 2147483647LL)
+    return set_error(DD_ERR_ARG, "dd_plan_dm_range: first trial index %d out of range", dm_index0);
   if (n_out <= 0) return set_error(DD_ERR_ARG, "dd_plan: n_out must be > 0");
   if (dtype != DD_U8_I32 && dtype != DD_F32_F32) return set_error(DD_ERR_ARG, "dd_plan: unknown dtype %d", (int)dtype);
   if (dtype == DD_U8_I32 && (int64_t)channels * 255 > 2147483647LL)
@@ -286,6 +294,7 @@ extern "C" dd_status dd_plan(dd_plan_t* out, int32_t channels, double f_low_mhz,
   p->t_samp = t_samp_s;
   p->dm_first = dm_first;
   p->dm_step = dm_step;
+  p->dm_index0 = dm_index0;
   p->dtype = dtype;
   dd_status st = compute_delay_table(*p);
   if (st != DD_OK) {

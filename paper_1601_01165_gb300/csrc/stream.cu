@@ -41,8 +41,8 @@ extern "C" dd_status dd_stream_create(dd_stream_t* out, dd_plan_t plan, int64_t 
   if (!out || !plan || chunk_len <= 0) return set_error(DD_ERR_ARG, "dd_stream_create: bad arguments");
   dd_stream_s* st = new (std::nothrow) dd_stream_s();
   if (!st) return set_error(DD_ERR_NOMEM, "dd_stream_create: host allocation failed");
-  dd_status s = dd_plan(&st->chunk_plan, plan->C, plan->f_low, plan->chan_bw, plan->t_samp, plan->dm_first,
-                        plan->dm_step, plan->n_dm, chunk_len, plan->dtype);
+  dd_status s = dd_plan_dm_range(&st->chunk_plan, plan->C, plan->f_low, plan->chan_bw, plan->t_samp, plan->dm_first,
+                                 plan->dm_step, plan->dm_index0, plan->n_dm, chunk_len, plan->dtype);
   if (s != DD_OK) {
     delete st;
     return s;

@@ -26,6 +26,8 @@ static std::string tune_key(const dd_plan_s& p) {
   std::snprintf(buf, sizeof(buf), "%s|C=%d|f_low=%.9g|chan_bw=%.9g|t_samp=%.9g|dm_first=%.9g|dm_step=%.9g|n_dm=%d|n_out=%lld|%s",
                 prop.name, p.C, p.f_low, p.chan_bw, p.t_samp, p.dm_first, p.dm_step, p.n_dm, (long long)p.n_out,
                 p.dtype == DD_U8_I32 ? "u8" : "f32");
+  if (p.dm_index0 != 0)  // a plan over trials [dm_index0, dm_index0 + n_dm) of the grid
+    std::snprintf(buf + std::strlen(buf), sizeof(buf) - std::strlen(buf), "|dm_index0=%d", p.dm_index0);
   return buf;
 }
 

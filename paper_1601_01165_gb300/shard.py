@@ -4,6 +4,12 @@ Beams are independent (Section 2), so N GPUs split a set of beams with no
 data exchange: each beam goes to exactly one rank, largest first onto the
 least-loaded rank (longest-processing-time order), where a beam's cost is
 channels x DM trials x output samples (Algorithm 1's d x s x c).
+
+One large beam splits by DM trials instead: every DM trial is its own sum
+over the channels (Algorithm 1), so rank r takes a contiguous block of
+trials (split_dm_range), builds the plan of that block (Plan.dm_range, whose
+rows equal the full plan's bit for bit), reads the whole input and writes its
+own output rows.  Nothing is exchanged or reduced.
 """
 from __future__ import annotations
 
@@ -28,3 +34,21 @@ def shard_beams(costs, world_size: int) -> list[list[int]]:
 
 def rank_beams(costs, world_size: int, rank: int) -> list[int]:
     return shard_beams(costs, world_size)[rank]
+
+
+def split_dm_range(n_dm: int, world_size: int, align: int = 1) -> list[tuple[int, int]]:
+    """Contiguous DM-trial blocks [i0, i1), one per rank, covering [0, n_dm)
+    once.  Interior boundaries are multiples of `align` (a kernel's trials per
+    block, so no block straddles two ranks); the blocks differ by at most one
+    `align` unit.  Ranks past the last unit get empty blocks (i0 == i1)."""
+    if world_size <= 0 or align <= 0 or n_dm < 0:
+        raise ValueError("world_size and align must be positive, n_dm non-negative")
+    units = -(-n_dm // align)
+    base, extra = divmod(units, world_size)
+    out, u = [], 0
+    for r in range(world_size):
+        k = base + (1 if r < extra else 0)
+        i0, i1 = min(u * align, n_dm), min((u + k) * align, n_dm)
+        out.append((i0, i1))
+        u += k
+    return out

@@ -202,3 +202,32 @@ def test_u8_saturated_sums_are_exact(dd, setup):
         assert plan.device_status() == 0
         ref, _ = oracle_window(d, x, "u8", 0, setup.n_dm, 0, setup.n_out)
         assert_parity(got, ref, None, "u8", where=f"{setup.name} {cfg}")
+
+
+@pytest.mark.parametrize("dtype", ["f32", "u8"])
+def test_dm_range_plans_tile_the_full_plan(dd, dtype):
+    """One beam split by DM trials (dd_plan_dm_range): the plans of blocks
+    [i0, i1) have the full plan's delay rows, and their outputs, stacked,
+    equal the full plan's output bit for bit, for blocks that start on and
+    off the kernels' trial tiles."""
+    from paper_1601_01165_gb300.shard import split_dm_range
+    s = synth.Setup("apertif-dm-split", 1024, 1420.0, 0.29296875, 50e-6, 0.0, 0.25, 100, 4500)
+    full = dd.Plan.from_setup(s, dtype)
+    d = full.delays()
+    x, _ = make_input(s, dtype, 11, full.n_in, full.padded_in_stride())
+    xt = torch.from_numpy(x).cuda()
+    ref = full.forward(xt).cpu().numpy()
+    for world, align in ((3, 6), (4, 1), (2, 64)):
+        parts = split_dm_range(s.n_dm, world, align)
+        rows = []
+        for i0, i1 in parts:
+            if i1 == i0:
+                continue
+            sub = dd.Plan.dm_range(s, i0, i1, dtype)
+            assert (sub.delays() == d[i0:i1]).all()
+            assert sub.n_in <= full.n_in
+            rows.append(sub.forward(xt).cpu().numpy())   # the whole input, as every rank holds it
+            assert sub.device_status() == 0
+        got = np.concatenate(rows)
+        assert got.shape == ref.shape
+        assert np.array_equal(got, ref), f"world {world} align {align}"
