@@ -47,7 +47,16 @@ __device__ double block_sum(double v, double* red) {
   return r;
 }
 
-// One block per row: mean, sd, best S/N and where it is.
+// One block per row: mean, sd, best S/N and where it is.  Each thread takes
+// a contiguous run of boxcar starts and slides the window, b[t] = b[t-1] +
+// (x[t+7] - x[t-1]) in double.  A sum of a few floats is exact in double while
+// the row's values span less than 2^26 in magnitude, so then b equals the
+// direct 8-term sum.  Pass 1: the sum of b and the largest b (first t);
+// pass 2: the variance about the mean; the best S/N is (b_max - mean) / sd
+// with one division.  S/N is monotonic in b, so the first maximum of S/N lies
+// among the starts whose b is within rounding of b_max; pass 3 takes the first
+// start up to that t whose S/N equals the best (a different t only when two
+// sums round to one S/N).
 template <int NT>
 __global__ void __launch_bounds__(NT) snr_rows_kernel(const float* __restrict__ x, int64_t stride, int64_t n_cols,
                                                       RowStat* __restrict__ stats) {
@@ -57,41 +66,84 @@ __global__ void __launch_bounds__(NT) snr_rows_kernel(const float* __restrict__ 
   const int i = blockIdx.x;
   const float* row = x + (int64_t)i * stride;
   const int64_t nb = n_cols - kBox + 1;
-  double s = 0.0;
-  for (int64_t t = threadIdx.x; t < nb; t += NT) s += boxcar(row, t);
-  const double mean = block_sum<NT>(s, red) / (double)nb;
-  double v = 0.0;
-  for (int64_t t = threadIdx.x; t < nb; t += NT) {
-    const double d = boxcar(row, t) - mean;
-    v += d * d;
-  }
-  const double sd = sqrt(block_sum<NT>(v, red) / (double)nb);
-  double zb = -DBL_MAX;
-  int64_t tb = -1;
-  if (sd > 0.0) {
-    for (int64_t t = threadIdx.x; t < nb; t += NT) {
-      const double z = (boxcar(row, t) - mean) / sd;
-      if (z > zb) {  // t increases along the loop, so the first maximum is kept
-        zb = z;
-        tb = t;
+  const int64_t per = (nb + NT - 1) / NT;
+  const int64_t t_begin = min(nb, (int64_t)threadIdx.x * per), t_end = min(nb, t_begin + per);
+
+  // pass 1: sum and largest boxcar
+  double s = 0.0, bmax = -DBL_MAX;
+  int64_t tmax = -1;
+  if (t_begin < t_end) {
+    double b = boxcar(row, t_begin);
+    for (int64_t t = t_begin;;) {
+      s += b;
+      if (b > bmax) {  // t increases, so the first maximum is kept
+        bmax = b;
+        tmax = t;
       }
+      if (++t >= t_end) break;
+      b += (double)__ldg(row + t + kBox - 1) - (double)__ldg(row + t - 1);
     }
   }
-  zbest[threadIdx.x] = zb;
-  tbest[threadIdx.x] = tb;
+  const double mean = block_sum<NT>(s, red) / (double)nb;
+  zbest[threadIdx.x] = bmax;
+  tbest[threadIdx.x] = tmax;
   __syncthreads();
   for (int h = NT / 2; h > 0; h >>= 1) {
     if ((int)threadIdx.x < h) {
-      const double zo = zbest[threadIdx.x + h];
+      const double bo = zbest[threadIdx.x + h];
       const int64_t to = tbest[threadIdx.x + h];
-      if (zo > zbest[threadIdx.x] || (zo == zbest[threadIdx.x] && to >= 0 && (tbest[threadIdx.x] < 0 || to < tbest[threadIdx.x]))) {
-        zbest[threadIdx.x] = zo;
+      if (to >= 0 && (tbest[threadIdx.x] < 0 || bo > zbest[threadIdx.x] ||
+                      (bo == zbest[threadIdx.x] && to < tbest[threadIdx.x]))) {
+        zbest[threadIdx.x] = bo;
         tbest[threadIdx.x] = to;
       }
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) stats[i] = RowStat{sd > 0.0 ? zbest[0] : -DBL_MAX, mean, sd, sd > 0.0 ? tbest[0] : -1};
+  const double b_top = zbest[0];
+  const int64_t t_top = tbest[0];
+  __syncthreads();
+
+  // pass 2: variance about the mean
+  double v = 0.0;
+  if (t_begin < t_end) {
+    double b = boxcar(row, t_begin);
+    for (int64_t t = t_begin;;) {
+      const double d = b - mean;
+      v += d * d;
+      if (++t >= t_end) break;
+      b += (double)__ldg(row + t + kBox - 1) - (double)__ldg(row + t - 1);
+    }
+  }
+  const double sd = sqrt(block_sum<NT>(v, red) / (double)nb);
+  if (!(sd > 0.0)) {
+    if (threadIdx.x == 0) stats[i] = RowStat{-DBL_MAX, mean, sd, -1};
+    return;
+  }
+  const double z_top = (b_top - mean) / sd;
+
+  // pass 3: the first start before t_top with the same S/N, if any
+  const double b_cut = b_top - 1e-12 * (fabs(b_top - mean) + fabs(b_top));
+  int64_t tf = t_top;
+  const int64_t t_stop = min(t_end, t_top);
+  if (t_begin < t_stop) {
+    double b = boxcar(row, t_begin);
+    for (int64_t t = t_begin;;) {
+      if (b >= b_cut && (b - mean) / sd == z_top) {
+        tf = t;
+        break;
+      }
+      if (++t >= t_stop) break;
+      b += (double)__ldg(row + t + kBox - 1) - (double)__ldg(row + t - 1);
+    }
+  }
+  tbest[threadIdx.x] = tf;
+  __syncthreads();
+  for (int h = NT / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) tbest[threadIdx.x] = min(tbest[threadIdx.x], tbest[threadIdx.x + h]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) stats[i] = RowStat{z_top, mean, sd, tbest[0]};
 }
 
 // One block: the best row (first on ties) -> result.
