@@ -120,14 +120,15 @@ void free_plan_device(dd_plan_s* p) {
 // Default configuration: the first valid entry of a preference list, in
 // the order measured on the Table 2 setups (Apertif float: TMW6 4.07 ms,
 // staged d8/t1024 4.94 ms; LOFAR float: staged d8/t1024 3.16 ms, d32/t384
-// 3.12 ms; Apertif uint8: U8PK c32 2.22 ms); dd_tune replaces it with a
+// 3.12 ms; Apertif uint8: U8PK 4 trials/warp c24 2.10 ms); dd_tune replaces it with a
 // measured choice.  TMW6 is offered only where a 6-trial group's offsets fit
 // its windows (Apertif, not LOFAR).
 static const char* const kPrefsF32[] = {"tmw6_f32_d6_t4096",     "staged_d8_t1024_c4_s3", "staged_d16_t512_c8_s3",
                                         "staged_d32_t512_c8_s2", "staged_d32_t384_c4_s3", "staged_d16_t256_c8_s3",
                                         "naive_t256"};
-static const char* const kPrefsU8[] = {"u8pk_w8x1_d2_c32_st3", "u8pk_w8x1_d2_c16_st4", "u8pk_w8x1_d4_c16_st3",
-                                       "staged_d16_t512_c8_s3", "staged_d8_t1024_c4_s3", "naive_t256"};
+static const char* const kPrefsU8[] = {"u8pk_w8x1_d4_c24_st3", "u8pk_w8x1_d4_c16_st3", "u8pk_w8x1_d2_c32_st3",
+                                       "u8pk_w8x1_d2_c16_st4", "staged_d16_t512_c8_s3", "staged_d8_t1024_c4_s3",
+                                       "naive_t256"};
 
 static int preferred(const dd_plan_s& p, bool staged_only) {
   const bool u8 = p.dtype == DD_U8_I32;

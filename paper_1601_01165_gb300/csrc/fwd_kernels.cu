@@ -364,27 +364,76 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
   if (st.copies()) st.prologue();
 
   uint32_t ra[DPW][KW], rb[DPW][KW];  // A and B of each word (see above)
-  int32_t tot[DPW][SPL];
 #pragma unroll
-  for (int m = 0; m < DPW; ++m) {
+  for (int m = 0; m < DPW; ++m)
 #pragma unroll
     for (int w = 0; w < KW; ++w) ra[m][w] = rb[m][w] = 0u;
-#pragma unroll
-    for (int q = 0; q < SPL; ++q) tot[m][q] = 0;
-  }
-  auto flush = [&]() {
+  const int lane_off = wt * 32 * SPL + lane * SPL;  // this lane's first sample in the tile
+  // Flush: decode the exact sums since the last flush and add them to the
+  // int32 totals, then clear A and B.  With up to two trials per warp the
+  // totals stay in registers and leave through a shared-memory transpose at
+  // the end; with four there is no room, so each flush adds them straight to
+  // the lane's own output samples (the first flush stores them; each lane
+  // owns SPL consecutive samples of its trials, so no other thread touches
+  // them; 16-byte accesses where the row allows).
+  constexpr bool kOutTotals = DPW >= 4;
+  int32_t tot[kOutTotals ? 1 : DPW][kOutTotals ? 1 : SPL];
+  if constexpr (!kOutTotals) {
 #pragma unroll
     for (int m = 0; m < DPW; ++m)
 #pragma unroll
-      for (int w = 0; w < KW; ++w) {
-        const uint32_t s1 = rb[m][w] & 0xffffu, s3 = rb[m][w] >> 16;
-        const uint32_t s02 = ra[m][w] - (s1 << 8) - (s3 << 24);  // S0 + 2^16 S2
-        tot[m][4 * w + 0] += (int32_t)(s02 & 0xffffu);
-        tot[m][4 * w + 1] += (int32_t)s1;
-        tot[m][4 * w + 2] += (int32_t)(s02 >> 16);
-        tot[m][4 * w + 3] += (int32_t)s3;
-        ra[m][w] = rb[m][w] = 0u;
+      for (int q = 0; q < SPL; ++q) tot[m][q] = 0;
+  }
+  int32_t* __restrict__ out = static_cast<int32_t*>(a.out);
+  const bool vec = (reinterpret_cast<uintptr_t>(a.out) % 16 == 0) && (a.out_stride % 4 == 0);
+  const int64_t tl = t0 + lane_off;
+  const int nl = (int)max((int64_t)0, min((int64_t)SPL, a.n_out - tl));  // this lane's samples inside the output
+  bool first = true;
+  auto flush = [&]() {
+    if constexpr (!kOutTotals) {
+#pragma unroll
+      for (int m = 0; m < DPW; ++m)
+#pragma unroll
+        for (int w = 0; w < KW; ++w) {
+          const uint32_t s1 = rb[m][w] & 0xffffu, s3 = rb[m][w] >> 16;
+          const uint32_t s02 = ra[m][w] - (s1 << 8) - (s3 << 24);  // S0 + 2^16 S2
+          tot[m][4 * w + 0] += (int32_t)(s02 & 0xffffu);
+          tot[m][4 * w + 1] += (int32_t)s1;
+          tot[m][4 * w + 2] += (int32_t)(s02 >> 16);
+          tot[m][4 * w + 3] += (int32_t)s3;
+          ra[m][w] = rb[m][w] = 0u;
+        }
+    } else {
+#pragma unroll
+      for (int m = 0; m < DPW; ++m) {
+        const int i = i0 + wd * DPW + m;
+        int32_t* o = out + (int64_t)min(i, a.n_dm - 1) * a.out_stride + tl;
+#pragma unroll
+        for (int w = 0; w < KW; ++w) {
+          const uint32_t s1 = rb[m][w] & 0xffffu, s3 = rb[m][w] >> 16;
+          const uint32_t s02 = ra[m][w] - (s1 << 8) - (s3 << 24);  // S0 + 2^16 S2
+          int4 v = make_int4((int32_t)(s02 & 0xffffu), (int32_t)s1, (int32_t)(s02 >> 16), (int32_t)s3);
+          ra[m][w] = rb[m][w] = 0u;
+          if (i >= a.n_dm) continue;
+          if (vec && 4 * w + 3 < nl) {
+            int4* p4 = reinterpret_cast<int4*>(o + 4 * w);
+            if (!first) {
+              const int4 u = *p4;
+              v.x += u.x, v.y += u.y, v.z += u.z, v.w += u.w;
+            }
+            *p4 = v;
+          } else {  // row end or unaligned rows: one sample at a time
+            int32_t* e = o + 4 * w;
+            const int k = nl - 4 * w;
+            if (k > 0) e[0] = first ? v.x : e[0] + v.x;
+            if (k > 1) e[1] = first ? v.y : e[1] + v.y;
+            if (k > 2) e[2] = first ? v.z : e[2] + v.z;
+            if (k > 3) e[3] = first ? v.w : e[3] + v.w;
+          }
+        }
       }
+    }
+    first = false;
   };
   // x + y * one with one == 1 at run time: an integer multiply-add (FMA pipe)
   const uint32_t one = a.C > 0 ? 1u : 0u;
@@ -399,7 +448,6 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
     asm("prmt.b32.f4e %0, %1, %2, %3;" : "=r"(d) : "r"(lo), "r"(hi), "r"(sel));
     return d;
   };
-  const int lane_off = wt * 32 * SPL + lane * SPL;  // this lane's first sample in the tile
   // Channel row j of stage s: the row and the offset `cj` such that trial
   // slot i's samples for this lane start at byte cj + dl[i] of the row (the
   // row starts at t0 + dl[0] rounded down to 16 bytes; t0 is a multiple of 16).
@@ -482,34 +530,35 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
     }
     stage_release(B, k, lane);
   }
-  flush();
+  if (ok) flush();
   if (st.copies()) st.drain();
   if (!ok && lane == 0) report_error(a.status, kDevWaitTimeout);
-
-  // transpose through shared memory (every warp is past the channel loop and
-  // no copy is in flight, so the stage area is free)
-  __syncthreads();
-  if (!ok) return;
-  int32_t* epi = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes) + (size_t)warp * DPW * 32 * SPL;
+  if constexpr (!kOutTotals) {
+    // transpose through shared memory (every warp is past the channel loop
+    // and no copy is in flight, so the stage area is free)
+    __syncthreads();
+    if (!ok) return;
+    int32_t* epi = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes) + (size_t)warp * DPW * 32 * SPL;
 #pragma unroll
-  for (int m = 0; m < DPW; ++m)
+    for (int m = 0; m < DPW; ++m)
 #pragma unroll
-    for (int q = 0; q < SPL; ++q) epi[m * 32 * SPL + lane * SPL + q] = tot[m][q];
-  __syncwarp();
-  int32_t* __restrict__ out = static_cast<int32_t*>(a.out);
-  const int tw0 = wt * 32 * SPL;
-  const int lim = min(32 * SPL, nt - tw0);
-  for (int m = 0; m < DPW; ++m) {
-    const int i = i0 + wd * DPW + m;
-    if (i >= a.n_dm) break;
-    int32_t* orow = out + (int64_t)i * a.out_stride + t0 + tw0;
-    for (int u = lane; u < lim; u += 32) orow[u] = epi[m * 32 * SPL + u];
+      for (int q = 0; q < SPL; ++q) epi[m * 32 * SPL + lane * SPL + q] = tot[m][q];
+    __syncwarp();
+    const int tw0 = wt * 32 * SPL;
+    const int lim = min(32 * SPL, nt - tw0);
+    for (int m = 0; m < DPW; ++m) {
+      const int i = i0 + wd * DPW + m;
+      if (i >= a.n_dm) break;
+      int32_t* orow = out + (int64_t)i * a.out_stride + t0 + tw0;
+      for (int u = lane; u < lim; u += 32) orow[u] = epi[m * 32 * SPL + u];
+    }
   }
 }
 
+// Stages, and with up to two trials per warp room for the final transpose.
 __host__ __device__ constexpr int u8pk_smem_bytes(int stages, int cc, int bd, int pitch, int nw, int dpw) {
-  return (stages * cc * pitch + stages * cc * bd * 4) > nw * dpw * 32 * 28 * 4
-             ? kStBarBytes + (stages * cc * pitch + stages * cc * bd * 4)
+  return (dpw >= 4 || stages * cc * pitch + stages * cc * bd * 4 > nw * dpw * 32 * 28 * 4)
+             ? kStBarBytes + stages * cc * pitch + stages * cc * bd * 4
              : kStBarBytes + nw * dpw * 32 * 28 * 4;
 }
 
@@ -554,7 +603,9 @@ static cudaError_t launch_staged_t(const TileConfig& cfg, const FwdArgs& a, cuda
   X(8, 1, 4, 16, 3)      \
   X(4, 1, 2, 32, 3)      \
   X(8, 2, 1, 16, 4)      \
-  X(8, 1, 2, 32, 3)
+  X(8, 1, 2, 32, 3)      \
+  X(8, 1, 4, 16, 4)      \
+  X(8, 1, 4, 24, 3)
 
 template <int WD, int WT, int DPW, int CC, int ST>
 static cudaError_t launch_u8pk_t(const TileConfig& cfg, const FwdArgs& a, cudaStream_t s) {
