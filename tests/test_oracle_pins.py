@@ -416,13 +416,14 @@ def test_oracle_adjoint_and_weight_gradient_pass_gradcheck():
     assert torch.autograd.gradcheck(OracleDD.apply, (x, w), eps=1e-3, atol=1e-4, rtol=1e-3)
 
 
-def test_packed_uint8_decode_is_exact_up_to_256_channels():
+def test_packed_uint8_decode_is_exact_within_16_bit_lanes():
     """The packed uint8 kernel keeps, per aligned word x = s0 + 2^8 s1 + 2^16 s2
     + 2^24 s3, the sum A of the words modulo 2^32 and the sum B of the odd
     bytes as two 16-bit lanes, and recovers S1, S3 = B's lanes and
     S0 + 2^16 S2 = A - 2^8 S1 - 2^24 S3 (mod 2^32).  Exact while every S_k
-    < 2^16, i.e. for up to 256 channels of 8-bit samples; checked here on
-    random, all-255 and all-0 words, and shown to fail at 257 channels of 255."""
+    < 2^16: for any 8-bit samples up to 257 channels (257 * 255 = 65535), so
+    the kernel's 256-channel periods are safe; checked on random, all-255 and
+    all-0 words, and shown to fail at 258 channels of 255."""
     rng = np.random.default_rng(7)
 
     def decode(words):
@@ -433,7 +434,7 @@ def test_packed_uint8_decode_is_exact_up_to_256_channels():
         s02 = (a - (s1 << 8) - (s3 << 24)) & 0xFFFFFFFF
         return [s02 & 0xFFFF, s1, s02 >> 16, s3], [int(v) for v in s.sum(axis=0)]
 
-    for n in (1, 2, 255, 256):
+    for n in (1, 2, 255, 256, 257):
         for kind in ("random", "max", "zero"):
             if kind == "random":
                 w = rng.integers(0, 2 ** 32, size=n, dtype=np.uint64)
@@ -441,5 +442,5 @@ def test_packed_uint8_decode_is_exact_up_to_256_channels():
                 w = np.full(n, 0xFFFFFFFF if kind == "max" else 0, dtype=np.uint64)
             got, want = decode(w)
             assert got == want, (n, kind)
-    got, want = decode(np.full(257, 0xFFFFFFFF, dtype=np.uint64))
-    assert got != want   # 257 * 255 >= 2^16: the 256-channel period is the limit
+    got, want = decode(np.full(258, 0xFFFFFFFF, dtype=np.uint64))
+    assert got != want   # 258 * 255 >= 2^16: a 16-bit lane overflows
