@@ -103,6 +103,13 @@ dd_status dd_plan_dm_range(dd_plan_t* out, int32_t channels, double f_low_mhz, d
 dd_status dd_delay_table(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
                          double dm_first, double dm_step, int32_t n_dm, int32_t* host_out);
 
+/* Host-only: the delay rows of trials [dm_index0, dm_index0 + n_dm) exactly
+ * as dd_plan_dm_range computes them (rows dm_index0 .. of dd_delay_table's
+ * full table).  Argument rules and errors as dd_plan_dm_range. */
+dd_status dd_delay_table_dm_range(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                                  double dm_first, double dm_step, int32_t dm_index0, int32_t n_dm,
+                                  int32_t* host_out);
+
 /* Free a plan and its device memory.  NULL is accepted.  The caller must not
  * destroy a plan while work enqueued with it may still run. */
 dd_status dd_plan_destroy(dd_plan_t plan);

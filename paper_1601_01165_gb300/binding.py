@@ -66,6 +66,7 @@ def _declare(lib):
         "dd_plan": (st, [ctypes.POINTER(vp), i32, dbl, dbl, dbl, dbl, dbl, i32, i64, st]),
         "dd_plan_dm_range": (st, [ctypes.POINTER(vp), i32, dbl, dbl, dbl, dbl, dbl, i32, i32, i64, st]),
         "dd_delay_table": (st, [i32, dbl, dbl, dbl, dbl, dbl, i32, vp]),
+        "dd_delay_table_dm_range": (st, [i32, dbl, dbl, dbl, dbl, dbl, i32, i32, vp]),
         "dd_plan_destroy": (st, [vp]),
         "dd_plan_info": (st, [vp, P64, P32, P64]),
         "dd_plan_delays": (st, [vp, vp]),
@@ -117,11 +118,12 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
-def delay_table(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm) -> np.ndarray:
-    """Eq. 1 delay table as libdd computes it (host only, no GPU needed)."""
+def delay_table(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm, dm_index0=0) -> np.ndarray:
+    """Eq. 1 delay table as libdd computes it (host only, no GPU needed): rows
+    of trials dm_index0 .. dm_index0 + n_dm - 1 of the DM grid."""
     out = np.empty((n_dm, channels), dtype=np.int32)
-    check(load().dd_delay_table(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm,
-                                out.ctypes.data_as(ctypes.c_void_p)), "dd_delay_table")
+    check(load().dd_delay_table_dm_range(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, dm_index0,
+                                         n_dm, out.ctypes.data_as(ctypes.c_void_p)), "dd_delay_table_dm_range")
     return out
 
 

@@ -247,10 +247,18 @@ static dd_status check_plan_args(int32_t channels, double f_low_mhz, double chan
 
 extern "C" dd_status dd_delay_table(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
                                     double dm_first, double dm_step, int32_t n_dm, int32_t* host_out) {
+  return dd_delay_table_dm_range(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, 0, n_dm, host_out);
+}
+
+extern "C" dd_status dd_delay_table_dm_range(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                                             double dm_first, double dm_step, int32_t dm_index0, int32_t n_dm,
+                                             int32_t* host_out) {
   clear_error();
   if (!host_out) return set_error(DD_ERR_ARG, "dd_delay_table: host_out is NULL");
   dd_status st = check_plan_args(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm);
   if (st != DD_OK) return st;
+  if (dm_index0 < 0 || (int64_t)dm_index0 + n_dm > 2147483647LL)
+    return set_error(DD_ERR_ARG, "dd_delay_table: first trial index %d out of range", dm_index0);
   dd_plan_s p;
   p.C = channels;
   p.n_dm = n_dm;
@@ -259,6 +267,7 @@ extern "C" dd_status dd_delay_table(int32_t channels, double f_low_mhz, double c
   p.t_samp = t_samp_s;
   p.dm_first = dm_first;
   p.dm_step = dm_step;
+  p.dm_index0 = dm_index0;
   st = compute_delay_table(p);
   if (st != DD_OK) return st;
   std::memcpy(host_out, p.delays.data(), p.delays.size() * sizeof(int32_t));

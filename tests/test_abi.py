@@ -44,6 +44,32 @@ def test_library_delay_table_equals_oracle(oracle, setup):
     assert got.dtype == np.int32 and (got == want).all()
 
 
+@pytest.mark.parametrize("setup", [synth.APERTIF, synth.LOFAR], ids=lambda s: s.name)
+def test_delay_table_dm_range_rows_equal_the_full_table(setup):
+    """A block of trials [i0, i1) of the DM grid (the rows one GPU computes
+    when a beam is split by DM trials) has exactly the full table's rows, for
+    blocks on and off the kernels' trial tiles."""
+    from paper_1601_01165_gb300.shard import split_dm_range
+    args = list(setup.plan_args()[:7])
+    full = binding.delay_table(*args)
+    blocks = split_dm_range(setup.n_dm, 3, 6) + split_dm_range(setup.n_dm, 7, 1) + [(1, 2), (setup.n_dm - 1, setup.n_dm)]
+    for i0, i1 in blocks:
+        if i1 == i0:
+            continue
+        sub = binding.delay_table(*args[:6], i1 - i0, dm_index0=i0)
+        assert (sub == full[i0:i1]).all(), (i0, i1)
+
+
+def test_delay_table_dm_range_argument_errors():
+    for i0 in (-1, 2 ** 31 - 2):
+        with pytest.raises(binding.DDError) as e:
+            binding.delay_table(4, 1400.0, 1.0, 1e-3, 0.0, 1.0, 4, dm_index0=i0)
+        assert e.value.name == "DD_ERR_ARG"
+    lib = binding.load()
+    h = ctypes.c_void_p()
+    assert lib.dd_plan_dm_range(ctypes.byref(h), 64, 1400.0, 1.0, 1e-3, 0.0, 1.0, -3, 32, 100, 1) == 1
+
+
 def test_delay_table_argument_errors():
     for bad in [(0, 1400.0, 1.0, 1e-3, 0.0, 1.0, 4), (4, 0.0, 1.0, 1e-3, 0.0, 1.0, 4),
                 (4, 1400.0, -1.0, 1e-3, 0.0, 1.0, 4), (4, 1400.0, 1.0, 0.0, 0.0, 1.0, 4),
