@@ -46,9 +46,9 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # keyed by (setup name, output samples, kernel config, dtype); valid only while
 # the kernel source hash matches.
 NCU_TRAFFIC = {
-    # profiles/fwd_tmw6_f32_apertif.md: 113.4 MB read + 128.7 MB written
+    # 113.4 MB read + 128.7 MB written
     ("apertif", 20000, "tmw6_f32_d6_t4096", "f32"): {"bytes": 242_039_296, "hash": "0c415d9b453f6fd2"},
-    # profiles/fwd_u8pk_u8_apertif.md: 33.0 MB read + 112.8 MB written
+    # 33.0 MB read + 112.8 MB written
     ("apertif", 20000, "u8pk_w8x1_d4_c24_st3", "u8"): {"bytes": 145_724_928, "hash": "0c415d9b453f6fd2"},
 }
 

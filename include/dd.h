@@ -268,7 +268,9 @@ dd_status dd_boxcar_snr(const float* x, int64_t row_stride, int32_t n_rows, int6
  *  - n_rows > DD_NOALLOC_MAX_ROWS is rejected with DD_ERR_SHAPE.
  *  - The first call on a device looks up that array's device address (once
  *    per device, with the device current); make that first call before any
- *    stream capture.
+ *    stream capture.  The address belongs to the device's context: after
+ *    cudaDeviceReset (or anything else that replaces the context) the next
+ *    call looks it up again, so that call too should come before any capture.
  *  - Every call on a device shares the one array and it keeps the previous
  *    call's contents; nothing in it needs to start at zero (each call writes
  *    every entry it reads).  Calls that can overlap on the GPU (different
@@ -323,10 +325,13 @@ dd_status dd_batch_destroy(dd_batch_t batch);
  * The plan's n_out is not used by streaming; the output length is chunk_len.
  * dd_stream_save / dd_stream_restore copy the state (tail + sample counter)
  * to / from a host buffer of dd_stream_state_bytes bytes, for checkpointing.
+ * dd_stream_reset zeroes the tail on `stream` (asynchronously, ordered after
+ * the pushes queued on that stream) and restarts the chunk count at 0; pushes
+ * on other streams must be ordered against it by the caller.
  */
 dd_status dd_stream_create(dd_stream_t* out, dd_plan_t plan, int64_t chunk_len);
 dd_status dd_stream_push(dd_stream_t st, const void* chunk, void* out, int64_t* out_t0, void* stream);
-dd_status dd_stream_reset(dd_stream_t st);
+dd_status dd_stream_reset(dd_stream_t st, void* stream);
 dd_status dd_stream_state_bytes(dd_stream_t st, int64_t* bytes);
 dd_status dd_stream_save(dd_stream_t st, void* host_buf, void* stream);
 dd_status dd_stream_restore(dd_stream_t st, const void* host_buf, void* stream);

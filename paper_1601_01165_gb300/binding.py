@@ -84,7 +84,7 @@ def _declare(lib):
         "dd_batch_destroy": (st, [vp]),
         "dd_stream_create": (st, [ctypes.POINTER(vp), vp, i64]),
         "dd_stream_push": (st, [vp, vp, vp, P64, vp]),
-        "dd_stream_reset": (st, [vp]),
+        "dd_stream_reset": (st, [vp, vp]),
         "dd_stream_state_bytes": (st, [vp, P64]),
         "dd_stream_save": (st, [vp, vp, vp]),
         "dd_stream_restore": (st, [vp, vp, vp]),
@@ -396,8 +396,8 @@ class Stream:
                                     _stream_handle(stream)), "dd_stream_push")
         return out, t0.value
 
-    def reset(self):
-        check(load().dd_stream_reset(self._h), "dd_stream_reset")
+    def reset(self, stream=None):
+        check(load().dd_stream_reset(self._h, _stream_handle(stream)), "dd_stream_reset")
 
     def state_bytes(self) -> int:
         n = ctypes.c_int64()

@@ -214,8 +214,8 @@ __global__ void snr_grad_kernel(const float* __restrict__ x, int64_t stride, int
   grad[(int64_t)r.best_row * grad_stride + u] = (float)(-acc);
 }
 
-dd_status boxcar_snr_launch(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols, dd_snr_result* result,
-                            float* grad, int64_t grad_stride, cudaStream_t s, void* scratch) {
+dd_status boxcar_snr_launch(const char* who, const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
+                            dd_snr_result* result, float* grad, int64_t grad_stride, cudaStream_t s, void* scratch) {
   constexpr int NT = 256;
   RowStat* stats = static_cast<RowStat*>(scratch);
   snr_rows_kernel<NT><<<n_rows, NT, 0, s>>>(x, row_stride, n_cols, stats);
@@ -229,17 +229,18 @@ dd_status boxcar_snr_launch(const float* x, int64_t row_stride, int32_t n_rows, 
       e = cudaGetLastError();
     }
   }
-  if (e != cudaSuccess) return set_cuda_error("dd_boxcar_snr: launch", e);
+  if (e != cudaSuccess) return set_error(DD_ERR_CUDA, "%s: launch: %s (%s)", who, cudaGetErrorString(e),
+                                         cudaGetErrorName(e));
   return DD_OK;
 }
 
-dd_status boxcar_snr_check(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
+dd_status boxcar_snr_check(const char* who, const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
                            const dd_snr_result* result, const float* grad, int64_t grad_stride) {
-  if (!x || !result) return set_error(DD_ERR_ARG, "dd_boxcar_snr: x/result is NULL");
-  if (n_rows <= 0) return set_error(DD_ERR_ARG, "dd_boxcar_snr: n_rows must be > 0");
-  if (n_cols < kBox) return set_error(DD_ERR_SHAPE, "dd_boxcar_snr: n_cols must be >= %d", kBox);
-  if (row_stride < n_cols) return set_error(DD_ERR_SHAPE, "dd_boxcar_snr: row_stride < n_cols");
-  if (grad && grad_stride < n_cols) return set_error(DD_ERR_SHAPE, "dd_boxcar_snr: grad_stride < n_cols");
+  if (!x || !result) return set_error(DD_ERR_ARG, "%s: x/result is NULL", who);
+  if (n_rows <= 0) return set_error(DD_ERR_ARG, "%s: n_rows must be > 0", who);
+  if (n_cols < kBox) return set_error(DD_ERR_SHAPE, "%s: n_cols must be >= %d", who, kBox);
+  if (row_stride < n_cols) return set_error(DD_ERR_SHAPE, "%s: row_stride < n_cols", who);
+  if (grad && grad_stride < n_cols) return set_error(DD_ERR_SHAPE, "%s: grad_stride < n_cols", who);
   return DD_OK;
 }
 
@@ -251,14 +252,14 @@ extern "C" dd_status dd_boxcar_snr(const float* x, int64_t row_stride, int32_t n
                                    dd_snr_result* result, float* grad, int64_t grad_stride, void* stream) {
   NvtxRange range("dd_boxcar_snr");
   clear_error();
-  dd_status st = boxcar_snr_check(x, row_stride, n_rows, n_cols, result, grad, grad_stride);
+  dd_status st = boxcar_snr_check("dd_boxcar_snr", x, row_stride, n_rows, n_cols, result, grad, grad_stride);
   if (st != DD_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   void* scratch = nullptr;
   const size_t bytes = (size_t)n_rows * sizeof(RowStat);
   if (cudaMallocAsync(&scratch, bytes, s) != cudaSuccess)
     return set_error(DD_ERR_NOMEM, "dd_boxcar_snr: cannot allocate %zu bytes of scratch", bytes);
-  st = boxcar_snr_launch(x, row_stride, n_rows, n_cols, result, grad, grad_stride, s, scratch);
+  st = boxcar_snr_launch("dd_boxcar_snr", x, row_stride, n_rows, n_cols, result, grad, grad_stride, s, scratch);
   cudaFreeAsync(scratch, s);
   return st;
 }
@@ -272,10 +273,31 @@ namespace dd {
 static __device__ __align__(256) RowStat g_noalloc_rows[DD_NOALLOC_MAX_ROWS];
 constexpr int kNoAllocMaxDevices = 64;
 static std::mutex g_noalloc_mu;
-static void* g_noalloc_addr[kNoAllocMaxDevices] = {};
+// per device: the context the address was looked up in, and the address
+struct NoAllocSlot {
+  void* ctx = nullptr;
+  void* addr = nullptr;
+};
+static NoAllocSlot g_noalloc[kNoAllocMaxDevices];
+
+typedef int (*CtxGetCurrentFn)(void**);
+// The driver's cuCtxGetCurrent, looked up once through the runtime.
+static CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(p);
+  });
+  return fn;
+}
 
 // Device address of g_noalloc_rows on the current device, looked up on the
-// first call for that device.
+// first call for that device, and again whenever the device's context has
+// changed since (after cudaDeviceReset the array lives in the new context).
 static dd_status noalloc_rows(void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -283,22 +305,32 @@ static dd_status noalloc_rows(void** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices)
     return set_error(DD_ERR_UNSUPPORTED, "dd_boxcar_snr_noalloc: device %d is beyond the %d supported", dev,
                      kNoAllocMaxDevices);
+  // make sure the device's primary context exists and is current
+  e = cudaFree(nullptr);
+  if (e != cudaSuccess) return set_cuda_error("dd_boxcar_snr_noalloc: context", e);
+  void* ctx = nullptr;
+  CtxGetCurrentFn get = ctx_get_current();
+  if (!get || get(&ctx) != 0 || !ctx)
+    return set_error(DD_ERR_CUDA, "dd_boxcar_snr_noalloc: cannot read the current context");
   std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_addr[dev]) {
+  NoAllocSlot& slot = g_noalloc[dev];
+  if (!slot.addr || slot.ctx != ctx) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_rows);
     if (e != cudaSuccess || !p) return set_cuda_error("dd_boxcar_snr_noalloc: cudaGetSymbolAddress", e);
-    g_noalloc_addr[dev] = p;
+    slot.ctx = ctx;
+    slot.addr = p;
   }
-  *out = g_noalloc_addr[dev];
+  *out = slot.addr;
   return DD_OK;
 }
 }  // namespace dd
 
 extern "C" dd_status dd_boxcar_snr_noalloc(const float* x, int64_t row_stride, int32_t n_rows, int64_t n_cols,
                                            dd_snr_result* result, float* grad, int64_t grad_stride, void* stream) {
+  NvtxRange range("dd_boxcar_snr_noalloc");
   clear_error();
-  dd_status st = boxcar_snr_check(x, row_stride, n_rows, n_cols, result, grad, grad_stride);
+  dd_status st = boxcar_snr_check("dd_boxcar_snr_noalloc", x, row_stride, n_rows, n_cols, result, grad, grad_stride);
   if (st != DD_OK) return st;
   if (n_rows > DD_NOALLOC_MAX_ROWS)
     return set_error(DD_ERR_SHAPE, "dd_boxcar_snr_noalloc: %d rows exceed the fixed scratch of %d rows", n_rows,
@@ -306,6 +338,6 @@ extern "C" dd_status dd_boxcar_snr_noalloc(const float* x, int64_t row_stride, i
   void* rows = nullptr;
   st = noalloc_rows(&rows);
   if (st != DD_OK) return st;
-  return boxcar_snr_launch(x, row_stride, n_rows, n_cols, result, grad, grad_stride,
+  return boxcar_snr_launch("dd_boxcar_snr_noalloc", x, row_stride, n_rows, n_cols, result, grad, grad_stride,
                            static_cast<cudaStream_t>(stream), rows);
 }

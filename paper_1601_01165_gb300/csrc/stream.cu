@@ -95,12 +95,14 @@ extern "C" dd_status dd_stream_push(dd_stream_t st, const void* chunk, void* out
   return DD_OK;
 }
 
-extern "C" dd_status dd_stream_reset(dd_stream_t st) {
+extern "C" dd_status dd_stream_reset(dd_stream_t st, void* stream) {
   clear_error();
   if (!st) return set_error(DD_ERR_ARG, "dd_stream_reset: NULL stream state");
+  // on the caller's stream, so that it is ordered after pushes queued there
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t bytes = (size_t)st->C * st->stride * st->elem;
-  cudaError_t e = cudaMemset(st->buf[0], 0, bytes);
-  if (e == cudaSuccess) e = cudaMemset(st->buf[1], 0, bytes);
+  cudaError_t e = cudaMemsetAsync(st->buf[0], 0, bytes, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st->buf[1], 0, bytes, s);
   if (e != cudaSuccess) return set_cuda_error("dd_stream_reset", e);
   st->cur = 0;
   st->pushed = 0;

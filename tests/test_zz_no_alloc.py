@@ -69,6 +69,21 @@ def test_noalloc_matches_allocating_entry_point_twice(lib):
         assert got[6] == 1 and got[5] == rows // 3
 
 
+def test_noalloc_accepts_the_maximum_row_count(lib):
+    # exactly DD_NOALLOC_MAX_ROWS rows fill the whole fixed scratch; the
+    # maximum sits in the last row, whose scratch entry is the array's last
+    g = torch.Generator(device="cpu").manual_seed(3)
+    x = torch.randn((MAX_ROWS, 16), generator=g)
+    x[MAX_ROWS - 1, 4:12] += 9.0
+    x = x.cuda()
+    ref_raw, ref_grad = _call(lib, "dd_boxcar_snr", x)
+    got_raw, got_grad = _call(lib, "dd_boxcar_snr_noalloc", x)
+    ref, got = _fields(ref_raw), _fields(got_raw)
+    assert got[4:] == ref[4:] and got[5] == MAX_ROWS - 1 and got[6] == 1
+    np.testing.assert_allclose(got[:4], ref[:4], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(got_grad.numpy(), ref_grad.numpy(), rtol=1e-6, atol=1e-9)
+
+
 def test_noalloc_rejects_too_many_rows(lib):
     x = torch.zeros((1, 16), device="cuda")
     res = torch.zeros(48, dtype=torch.uint8, device="cuda")
