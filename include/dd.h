@@ -122,6 +122,18 @@ dd_status dd_plan_destroy(dd_plan_t plan);
  */
 dd_status dd_plan_info(dd_plan_t plan, int64_t* n_in, int32_t* max_delay, int64_t* device_bytes);
 
+/*
+ * The input row stride (elements, >= n_in) that every forward configuration
+ * of the plan takes at full speed: for float32, a multiple of 32 floats with
+ * at least 28 spare floats after the n_in samples read (the 9-trial Tensor
+ * Memory kernel loads 4-float-aligned 128-byte rows that may reach past
+ * n_in; the spare floats are read, never used); for uint8, n_in rounded up to
+ * 128 bytes.  Other strides >= n_in are accepted and run the fastest
+ * configuration that takes them.  Section 2.1: n_in = n_out + max_delay
+ * samples per channel.
+ */
+dd_status dd_plan_in_stride(dd_plan_t plan, int64_t* in_row_stride);
+
 /* Copy the plan's delay table (Eq. 1, in samples) to host memory `host_out`,
  * row-major [n_dm][channels] int32.  For checking the plan against Eq. 1. */
 dd_status dd_plan_delays(dd_plan_t plan, int32_t* host_out);

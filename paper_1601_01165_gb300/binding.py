@@ -70,6 +70,7 @@ def _declare(lib):
         "dd_plan_destroy": (st, [vp]),
         "dd_plan_info": (st, [vp, P64, P32, P64]),
         "dd_plan_delays": (st, [vp, vp]),
+        "dd_plan_in_stride": (st, [vp, P64]),
         "dd_plan_num_configs": (st, [vp, P32]),
         "dd_plan_config_name": (ctypes.c_char_p, [vp, i32]),
         "dd_plan_select_config": (st, [vp, i32]),
@@ -239,9 +240,10 @@ class Plan:
         return torch.zeros((self.channels, stride), dtype=self.in_dtype, device=self.device)
 
     def padded_in_stride(self) -> int:
-        """Row stride (elements) giving 128-byte input rows, which every kernel accepts."""
-        v = 128 if self.dtype == "u8" else 32
-        return (self.n_in + v - 1) // v * v
+        """Row stride (elements) that every kernel of the plan takes at full speed (dd_plan_in_stride)."""
+        n = ctypes.c_int64()
+        check(load().dd_plan_in_stride(self._h, ctypes.byref(n)), "dd_plan_in_stride")
+        return n.value
 
     def forward(self, x, w=None, out=None, stream=None):
         """out[i][t] = sum_c w[c] x[c][t + delay(c, i)] on the GPU (Algorithm 1)."""

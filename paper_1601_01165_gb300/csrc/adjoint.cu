@@ -105,7 +105,7 @@ extern "C" dd_status dd_adjoint(dd_plan_t plan, const float* grad_out, int64_t g
 
   // zero-padded copy of grad_out: P[i][max_d + t] = grad_out[i][t]
   if (!plan->adj_pad) {
-    const int64_t stride = (q->n_in + 3) / 4 * 4;
+    const int64_t stride = plan_in_stride(*q);  // the transposed plan's kernels take it at full speed
     const size_t bytes = (size_t)plan->n_dm * stride * sizeof(float);
     if (cudaMalloc(&plan->adj_pad, bytes) != cudaSuccess) {
       plan->adj_pad = nullptr;

@@ -43,12 +43,14 @@ static dd_status launch_range(dd_plan_s* p, const void* in, int64_t in_stride, c
   FwdArgs a{};
   a.in = in;
   a.in_stride = in_stride;
+  a.in_avail = in_stride - t0;
   a.w = w;
   a.out = out;
   a.out_stride = out_stride;
   a.delays = p->d_delays;
   a.delaysT = p->d_delaysT;
   a.hex_desc = p->d_hex_desc;
+  a.nine_desc = p->d_nine_desc;
   a.C = p->C;
   a.n_dm = p->n_dm;
   a.n_dm_pad = p->n_dm_pad;
@@ -66,7 +68,12 @@ static dd_status launch_range(dd_plan_s* p, const void* in, int64_t in_stride, c
     return nullptr;
   };
   if (cfg->kind != Kind::Naive && !aligned) cfg = first_of(Kind::Naive);
+  // TMW9 needs spare samples after each row, else TMW6 (if offered) takes it;
   // TMW6 stages 128-byte rows; other layouts take the preferred shared-memory kernel
+  if (cfg->kind == Kind::TmW9 && !tmw9_accepts(in, in_stride, a.n_in)) {
+    const TileConfig* t6 = first_of(Kind::TmW6);
+    cfg = t6 ? t6 : &p->configs[p->fallback];
+  }
   if (cfg->kind == Kind::TmW6 && !tmw6_accepts(in, in_stride)) cfg = &p->configs[p->fallback];
   cudaError_t e = launch_forward(*cfg, p->dtype, a, stream);
   if (e != cudaSuccess) return set_cuda_error("dd_forward: launch", e);
@@ -130,8 +137,8 @@ extern "C" dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_
     return set_error(DD_ERR_UNSUPPORTED, "dd_forward_host: uint8 plans take unit weights only");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t elem = plan->dtype == DD_U8_I32 ? 1 : 4;
-  // device rows padded to 128 bytes so every staged kernel applies
-  const int64_t dev_in_stride = (plan->n_in * (int64_t)elem + 127) / 128 * 128 / (int64_t)elem;
+  // device rows padded so that every configuration applies
+  const int64_t dev_in_stride = plan_in_stride(*plan);
   const size_t in_bytes = (size_t)plan->C * dev_in_stride * elem;
   const size_t out_bytes = (size_t)plan->n_dm * plan->n_out * 4;
   if (plan->h_in_bytes < in_bytes) {

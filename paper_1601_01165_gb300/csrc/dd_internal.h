@@ -24,8 +24,9 @@ struct NvtxRange {
 // the 2-D (DM x time) block of Section 2.2 with each channel's input span
 // staged in shared memory by bulk copies; U8PK is the uint8 path with packed
 // 16-bit integer sums; TMW6 (float) shares each channel's input window among
-// 6 DM trials through Tensor Memory.
-enum class Kind : int { Naive = 0, Staged = 1, U8Pk = 4, TmW6 = 7 };
+// 6 DM trials through Tensor Memory; TMW9 (float) shares it among 9 trials
+// and copies windows at 4-float granularity.
+enum class Kind : int { Naive = 0, Staged = 1, U8Pk = 4, TmW6 = 7, TmW9 = 9 };
 
 struct TileConfig {
   Kind kind;
@@ -44,12 +45,14 @@ struct TileConfig {
 struct FwdArgs {
   const void* in;
   int64_t in_stride;
+  int64_t in_avail;        // elements from `in` to the end of its row (in_stride - the launch's first sample)
   const float* w;
   void* out;
   int64_t out_stride;
   const int32_t* delays;   // [n_dm][C]
   const int32_t* delaysT;  // [C][n_dm_pad], DMs >= n_dm repeat the last trial
   const int4* hex_desc;    // 6-trial group descriptors [ceil(n_dm / 6)][C], or null
+  const int4* nine_desc;   // 9-trial group descriptors [ceil(n_dm / 9)][C], or null
   int32_t C;
   int32_t n_dm;
   int32_t n_dm_pad;
@@ -64,6 +67,11 @@ void apply_tune_db(dd_plan_s* plan);
 
 // TMW6 needs 16-byte aligned input rows of a multiple of 32 floats (128 bytes).
 bool tmw6_accepts(const void* in, int64_t in_stride);
+// TMW9 needs a 16-byte aligned input whose rows hold every needed sample in
+// whole 32-float rows of each of its eight tensor-map views (28 spare floats
+// per row are enough); tmw9_min_in_stride gives the smallest such stride.
+bool tmw9_accepts(const void* in, int64_t in_stride, int64_t n_in);
+int64_t tmw9_min_in_stride(int64_t n_in);
 
 // Forward launch on a given configuration.
 cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
@@ -87,6 +95,12 @@ constexpr int kDmPad = 64;
 // TMW6: the largest offset between a 6-trial group's first and last trial
 // that its Tensor Memory windows can hold.
 constexpr int kW6MaxOff = 31;
+// TMW9: the same for a 9-trial group.
+constexpr int kW9MaxOff = 31;
+
+// Input row stride (elements) that every forward configuration of a plan
+// takes: float rows with TMW9's spare samples, uint8 rows of 128 bytes.
+int64_t plan_in_stride(const dd_plan_s& p);
 
 }  // namespace dd
 
@@ -102,6 +116,7 @@ struct dd_plan_s {
   int32_t* d_delays = nullptr;        // [n_dm][C]
   int32_t* d_delaysT = nullptr;       // [C][n_dm_pad]
   int4* d_hex_desc = nullptr;         // [ceil(n_dm / 6)][C], float plans whose offsets fit a window
+  int4* d_nine_desc = nullptr;        // [ceil(n_dm / 9)][C], likewise for 9-trial groups
   int* d_status = nullptr;            // device error word
   int64_t device_bytes = 0;
   std::vector<dd::TileConfig> configs;

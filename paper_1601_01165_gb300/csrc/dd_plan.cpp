@@ -16,6 +16,7 @@ namespace dd {
 std::vector<TileConfig> staged_menu(dd_dtype dtype);
 std::vector<TileConfig> u8pk_menu(dd_dtype dtype);
 std::vector<TileConfig> tmw6_menu(dd_dtype dtype);
+std::vector<TileConfig> tmw9_menu(dd_dtype dtype);
 int u8pk_smem_for(const TileConfig& cfg, int pitch);
 int staged_smem_for(dd_dtype dtype, int stages, int cc, int bd, int pitch);
 
@@ -87,12 +88,49 @@ static int32_t build_hex_desc(const dd_plan_s& p, std::vector<int4>& desc) {
   return worst;
 }
 
+// Descriptor of (channel c, group of 9 trials starting at 9g), group-major
+// ([g][c]), for windows that start at the 4-float boundary at or below the
+// group's first sample: x = delay of the group's first trial; bytes 0..2 of
+// y, z, w = the column of the first sample of trials 0..2, 3..5, 6..8 in the
+// window, (x & 3) + offset (the warp reading trials 3p..3p+2 takes word p);
+// byte 3 of y = the window's 4-float chunks, ceil(((x & 3) + 32 + largest
+// offset) / 4).  Returns the largest offset seen.
+static int32_t build_nine_desc(const dd_plan_s& p, std::vector<int4>& desc) {
+  const int32_t n_g = (p.n_dm + 8) / 9;
+  desc.assign((size_t)p.C * n_g, int4{0, 0, 0, 0});
+  int32_t worst = 0;
+  for (int32_t c = 0; c < p.C; ++c) {
+    for (int32_t g = 0; g < n_g; ++g) {
+      const int32_t base = p.delays[(size_t)(9 * g) * p.C + c];
+      const int32_t sh = base & 3;
+      uint32_t word[3] = {0, 0, 0};
+      int32_t mx = 0;
+      for (int j = 0; j < 9; ++j) {
+        const int32_t i = std::min(9 * g + j, p.n_dm - 1);
+        const int32_t o = p.delays[(size_t)i * p.C + c] - base;
+        mx = std::max(mx, o);
+        word[j / 3] |= (uint32_t)std::min(sh + o, 255) << (8 * (j % 3));
+      }
+      worst = std::max(worst, mx);
+      const uint32_t nch = (uint32_t)std::min((sh + 32 + mx + 3) / 4, 255);
+      desc[(size_t)g * p.C + c] = int4{base, (int)(word[0] | nch << 24), (int)word[1], (int)word[2]};
+    }
+  }
+  return worst;
+}
+
 int32_t block_spread_of(const dd_plan_s& p, int bd) { return block_spread(p, bd); }
+
+int64_t plan_in_stride(const dd_plan_s& p) {
+  if (p.dtype == DD_U8_I32) return (p.n_in + 127) / 128 * 128;
+  return tmw9_min_in_stride(p.n_in);
+}
 
 void free_plan_device(dd_plan_s* p) {
   cudaFree(p->d_delays);
   cudaFree(p->d_delaysT);
   cudaFree(p->d_hex_desc);
+  cudaFree(p->d_nine_desc);
   cudaFree(p->d_status);
   cudaFree(p->h_dev_in);
   cudaFree(p->h_dev_out);
@@ -110,6 +148,7 @@ void free_plan_device(dd_plan_s* p) {
   }
   p->d_delays = p->d_delaysT = nullptr;
   p->d_hex_desc = nullptr;
+  p->d_nine_desc = nullptr;
   p->d_status = nullptr;
   p->h_dev_in = p->h_dev_out = nullptr;
   p->h_dev_w = nullptr;
@@ -118,12 +157,13 @@ void free_plan_device(dd_plan_s* p) {
 }
 
 // Default configuration: the first valid entry of a preference list, in
-// the order measured on the Table 2 setups (Apertif float: TMW6 4.07 ms,
+// the order measured on the Table 2 setups (Apertif float: TMW9, TMW6 4.07 ms,
 // staged d8/t1024 4.94 ms; LOFAR float: staged d8/t1024 3.16 ms, d32/t384
 // 3.12 ms; Apertif uint8: U8PK 4 trials/warp c24 2.10 ms); dd_tune replaces it with a
 // measured choice.  TMW6 is offered only where a 6-trial group's offsets fit
 // its windows (Apertif, not LOFAR).
-static const char* const kPrefsF32[] = {"tmw6_f32_d6_t4096",     "staged_d8_t1024_c4_s3", "staged_d16_t512_c8_s3",
+static const char* const kPrefsF32[] = {"tmw9_f32_d9_t4096",     "tmw6_f32_d6_t4096",     "staged_d8_t1024_c4_s3",
+                                        "staged_d16_t512_c8_s3",
                                         "staged_d32_t512_c8_s2", "staged_d32_t384_c4_s3", "staged_d16_t256_c8_s3",
                                         "naive_t256"};
 static const char* const kPrefsU8[] = {"u8pk_w8x1_d4_c24_st3", "u8pk_w8x1_d4_c16_st3", "u8pk_w8x1_d2_c32_st3",
@@ -190,6 +230,22 @@ dd_status finish_plan(dd_plan_s* p) {
       hex_ok = true;
     }
   }
+  bool nine_ok = false;
+  if (p->dtype == DD_F32_F32) {
+    std::vector<int4> desc9;
+    if (build_nine_desc(*p, desc9) <= kW9MaxOff) {
+      const size_t bytes9 = desc9.size() * sizeof(int4);
+      e = cudaMalloc(&p->d_nine_desc, bytes9);
+      if (e == cudaSuccess) e = cudaMemcpy(p->d_nine_desc, desc9.data(), bytes9, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        free_plan_device(p);
+        return e == cudaErrorMemoryAllocation ? set_error(DD_ERR_NOMEM, "dd_plan: device allocation failed")
+                                              : set_cuda_error("dd_plan: upload", e);
+      }
+      p->device_bytes += (int64_t)bytes9;
+      nine_ok = true;
+    }
+  }
 
   // configuration menu, filtered by what this geometry allows
   const int V = p->dtype == DD_U8_I32 ? 16 : 4;
@@ -219,6 +275,12 @@ dd_status finish_plan(dd_plan_s* p) {
   if (hex_ok) {
     for (TileConfig cfg : tmw6_menu(p->dtype)) {
       if ((p->n_out + cfg.bt - 1) / cfg.bt > 65535) continue;  // time tiles are the grid's y
+      p->configs.push_back(cfg);
+    }
+  }
+  if (nine_ok) {
+    for (TileConfig cfg : tmw9_menu(p->dtype)) {
+      if ((p->n_out + cfg.bt - 1) / cfg.bt > 65535) continue;
       p->configs.push_back(cfg);
     }
   }
@@ -339,6 +401,13 @@ extern "C" dd_status dd_plan_info(dd_plan_t plan, int64_t* n_in, int32_t* max_de
   if (n_in) *n_in = plan->n_in;
   if (max_delay) *max_delay = plan->max_delay;
   if (device_bytes) *device_bytes = plan->device_bytes;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_in_stride(dd_plan_t plan, int64_t* in_row_stride) {
+  clear_error();
+  if (!plan || !in_row_stride) return set_error(DD_ERR_ARG, "dd_plan_in_stride: NULL argument");
+  *in_row_stride = plan_in_stride(*plan);
   return DD_OK;
 }
 

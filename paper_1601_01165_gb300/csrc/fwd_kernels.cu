@@ -640,6 +640,7 @@ static cudaError_t launch_staged(const TileConfig& cfg, const FwdArgs& a, cudaSt
 }
 
 cudaError_t launch_tmw6(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_tmw9(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s);
 
 cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s) {
   const bool weighted = a.w != nullptr;
@@ -652,6 +653,8 @@ cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs&
       return weighted ? launch_staged<float, true>(cfg, a, s) : launch_staged<float, false>(cfg, a, s);
     case Kind::TmW6:
       return launch_tmw6(cfg, dtype, a, s);
+    case Kind::TmW9:
+      return launch_tmw9(cfg, dtype, a, s);
     case Kind::U8Pk:
       if (dtype != DD_U8_I32 || weighted) return cudaErrorInvalidConfiguration;
       return launch_u8pk(cfg, a, s);

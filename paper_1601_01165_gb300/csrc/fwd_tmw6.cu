@@ -355,11 +355,12 @@ bool tmw6_accepts(const void* in, int64_t in_stride) {
   return in_stride % 32 == 0 && (reinterpret_cast<uintptr_t>(in) % 16) == 0 && encode_fn() != nullptr;
 }
 
-// Tensor map over the float input viewed as [C][in_stride / 32 rows][32]: one
+// Tensor map over the float input viewed as [C][in_avail / 32 rows][32]: one
 // load brings `rows` consecutive 128-byte rows of one channel, stored with
-// the 128-byte swizzle; rows past the end read as zero.
+// the 128-byte swizzle; rows past the end of the channel's row (measured from
+// `in`, which a time-chunked launch advances) read as zero.
 static bool encode_row_tiles(CUtensorMap* tm, const FwdArgs& a, int rows) {
-  const cuuint64_t dims[3] = {32, (cuuint64_t)(a.in_stride / 32), (cuuint64_t)a.C};
+  const cuuint64_t dims[3] = {32, (cuuint64_t)(a.in_avail / 32), (cuuint64_t)a.C};
   const cuuint64_t strides[2] = {128, (cuuint64_t)a.in_stride * 4};
   const cuuint32_t box[3] = {32, (cuuint32_t)rows, 1};
   const cuuint32_t es[3] = {1, 1, 1};
@@ -372,7 +373,8 @@ static bool encode_row_tiles(CUtensorMap* tm, const FwdArgs& a, int rows) {
 
 cudaError_t launch_tmw6(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s) {
   (void)cfg;
-  if (dtype != DD_F32_F32 || !tmw6_accepts(a.in, a.in_stride) || a.hex_desc == nullptr)
+  if (dtype != DD_F32_F32 || !tmw6_accepts(a.in, a.in_stride) || a.hex_desc == nullptr || a.in_avail % 32 != 0 ||
+      a.in_avail < a.n_in)
     return cudaErrorInvalidConfiguration;
   CUtensorMap tm;
   if (!encode_row_tiles(&tm, a, kQRows)) return cudaErrorInvalidValue;

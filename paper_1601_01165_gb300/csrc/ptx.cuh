@@ -151,6 +151,42 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
       : "r"(taddr)
       : "memory");
 }
+
+// Each thread loads 8 consecutive 32-bit columns of its own lane.  No memory
+// clobber: the load touches only Tensor Memory and the named registers.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
+               : "r"(taddr));
+}
+
+// Wait for this thread's Tensor Memory loads, naming the 24 registers the
+// last loads wrote as operands, so that no use of them can be scheduled
+// before the wait.
+__device__ __forceinline__ void tmem_wait_ld24(float* v) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
+                 "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
+                 "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),
+                 "+f"(v[22]), "+f"(v[23])
+               :
+               : "memory");
+}
+
+// One 16-byte chunk of this thread's lane to 4 consecutive columns.
+__device__ __forceinline__ void tmem_st4(uint32_t taddr, float4 x) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "f"(x.x), "f"(x.y),
+               "f"(x.z), "f"(x.w));
+}
+
+// Four 16-byte chunks of this thread's lane to 16 consecutive columns.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, float4 x0, float4 x1, float4 x2, float4 x3) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "f"(x0.x), "f"(x0.y), "f"(x0.z), "f"(x0.w), "f"(x1.x), "f"(x1.y), "f"(x1.z), "f"(x1.w), "f"(x2.x), "f"(x2.y),
+      "f"(x2.z), "f"(x2.w), "f"(x3.x), "f"(x3.y), "f"(x3.z), "f"(x3.w));
+}
 }  // namespace dd
 
 // -------------------------------------------------------------- TMA tiles

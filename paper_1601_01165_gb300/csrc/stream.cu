@@ -22,7 +22,7 @@ struct dd_stream_s {
   int32_t max_d = 0;
   int32_t C = 0;
   int elem = 4;
-  int64_t stride = 0;              // elements per buffer row (>= max_d + n, 128-byte multiple)
+  int64_t stride = 0;              // elements per buffer row (>= max_d + n, the chunk plan's input stride)
   void* buf[2] = {nullptr, nullptr};
   int cur = 0;
   int64_t pushed = 0;
@@ -55,8 +55,8 @@ extern "C" dd_status dd_stream_create(dd_stream_t* out, dd_plan_t plan, int64_t 
   st->max_d = plan->max_delay;
   st->C = plan->C;
   st->elem = plan->dtype == DD_U8_I32 ? 1 : 4;
-  const int64_t v = 128 / st->elem;  // 128-byte rows: every configuration takes the buffer
-  st->stride = (st->max_d + chunk_len + v - 1) / v * v;
+  // rows padded so that every configuration of the chunk plan takes the buffer
+  st->stride = plan_in_stride(*st->chunk_plan);
   const size_t bytes = (size_t)st->C * st->stride * st->elem;
   cudaError_t e = cudaMalloc(&st->buf[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&st->buf[1], bytes);
