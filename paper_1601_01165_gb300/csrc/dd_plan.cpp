@@ -246,7 +246,6 @@ dd_status finish_plan(dd_plan_s* p) {
       nine_ok = true;
     }
   }
-
   // configuration menu, filtered by what this geometry allows
   const int V = p->dtype == DD_U8_I32 ? 16 : 4;
   for (TileConfig cfg : staged_menu(p->dtype)) {

@@ -655,6 +655,7 @@ cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs&
       return launch_tmw6(cfg, dtype, a, s);
     case Kind::TmW9:
       return launch_tmw9(cfg, dtype, a, s);
+
     case Kind::U8Pk:
       if (dtype != DD_U8_I32 || weighted) return cudaErrorInvalidConfiguration;
       return launch_u8pk(cfg, a, s);

@@ -24,17 +24,18 @@
 //    rows r, r + 1, r + 2: compile-time shared addresses (128-byte swizzle,
 //    conflict-free 16-byte loads), n = ceil(((d0 mod 4) + 32 + max offset) / 4).
 //  * 12 warps, 3 per quadrant; warp p of a quadrant owns trials 3p..3p+2.
-//    Per channel it reads its trials' 32 columns in four phases of 8
-//    (tcgen05.ld.32x32b.x8, three trials per phase): it waits for a phase's
-//    loads, issues the next phase's, and adds the waited-for values (packed
-//    pairs, add.rn.f32x2: two IEEE adds per instruction), so every load is in
-//    flight during a phase of adds.  Trial columns come straight from the
-//    block's descriptor row in global memory (L1-resident), read a channel
-//    ahead: no cross-warp bookkeeping.
+//    Per channel it reads its trials' 32 columns in six phases of 16
+//    (tcgen05.ld.32x32b.x16, one trial per phase, trials in turn): it waits
+//    for a phase's load, issues the next phase's, and adds the waited-for
+//    values (packed pairs, add.rn.f32x2: two IEEE adds per instruction), so
+//    every load is in flight during a phase of adds.  Trial columns come
+//    straight from the block's descriptor row in global memory (L1-resident),
+//    read a channel ahead and broadcast from lane 0, so the compiler keeps
+//    the TMEM addresses in uniform registers: no cross-warp bookkeeping.
 //  * Warp p writes the window of channel p of the next step while it works on
-//    channel p of the current step (the three warps of a sub-partition copy
-//    at different times), from its private TMA stage; it then reloads the
-//    stage with its channel nine later.
+//    the step's middle channel, from its private TMA stage (four 16-byte
+//    chunks per 16-column TMEM store); it then reloads the stage with its
+//    channel nine later.
 //  * The quadrant's three warps meet at a named barrier between steps, after
 //    the last loads of the step have been waited for and before the next
 //    step's first loads are issued: the next windows are then in TMEM and
@@ -60,8 +61,6 @@ namespace {
 
 constexpr int kT = 9;                     // DM trials per block
 constexpr int kTPW = 3;                   // trials per warp
-constexpr int kPH = 8;                    // columns per load phase
-constexpr int kNPH = 32 / kPH;            // phases per channel
 constexpr int kQRows = 34;                // tile rows per quadrant: 32 lanes + 2 (a window spans <= 17 chunks)
 constexpr int kTileBytes = kQRows * 128;  // 4352
 constexpr int kStage = 5 * 1024;          // whole 1024-byte swizzle atoms
@@ -95,18 +94,20 @@ static_assert(sizeof(Hdr) <= kHdr, "header fits");
 // which is rbase(y) ^ (x << 4) with rbase(y) = y * 128 + ((y & 7) << 4).
 __device__ __forceinline__ uint32_t rbase(int y) { return (uint32_t)y * 128u + ((uint32_t)(y & 7) << 4); }
 
-// Chunks X0..X0+3 of one tile row to 16 TMEM columns, each 16-byte load
-// straight to 4 columns.
+// Chunks X0..X0+3 of one tile row to 16 TMEM columns in one store.
 template <int X0>
 __device__ __forceinline__ void copy4(const unsigned char* tile, uint32_t rb, uint32_t taddr) {
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    tmem_st4(taddr + 4 * k, *reinterpret_cast<const float4*>(tile + (rb ^ (uint32_t)((X0 + k) << 4))));
+  const float4 v0 = *reinterpret_cast<const float4*>(tile + (rb ^ (uint32_t)((X0 + 0) << 4)));
+  const float4 v1 = *reinterpret_cast<const float4*>(tile + (rb ^ (uint32_t)((X0 + 1) << 4)));
+  const float4 v2 = *reinterpret_cast<const float4*>(tile + (rb ^ (uint32_t)((X0 + 2) << 4)));
+  const float4 v3 = *reinterpret_cast<const float4*>(tile + (rb ^ (uint32_t)((X0 + 3) << 4)));
+  tmem_st16(taddr, v0, v1, v2, v3);
 }
 
-// Warp p's three trial columns (bytes 0..2 of word 1 + p of a descriptor).
+// Warp p's three trial columns (bytes 0..2 of word 1 + p of a descriptor),
+// broadcast from lane 0 (the same for every lane).
 __device__ __forceinline__ uint32_t warp_cols(const int4* d, int p) {
-  return __ldg(reinterpret_cast<const uint32_t*>(d) + 1 + p);
+  return __shfl_sync(0xffffffffu, __ldg(reinterpret_cast<const uint32_t*>(d) + 1 + p), 0);
 }
 
 }  // namespace
@@ -117,6 +118,14 @@ struct Tmw9Maps {
   CUtensorMap m[kMaps];
 };
 
+// Load phases of one channel: six, each loading 16 columns of one trial
+// (tcgen05.ld.32x32b.x16), trials in turn: phase f reads trial f % 3,
+// columns 16 (f / 3) .. + 16.
+constexpr int kPH = 16;
+constexpr int kNPH = 6;
+__device__ constexpr int ph_trial(int f) { return f % 3; }
+__device__ constexpr int ph_col(int f) { return 16 * (f / 3); }
+
 template <bool WEIGHTED>
 __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_constant__ Tmw9Maps maps, FwdArgs a) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -124,7 +133,11 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   const uint32_t sbase = smem_u32(smem_raw);
   unsigned char* stages = smem_raw + (((sbase + kHdr + 1023u) & ~1023u) - sbase);
 
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31;
+  // warp-uniform values go through a lane-0 broadcast, which lets the
+  // compiler keep them (and the TMEM addresses built from them) in uniform
+  // registers instead of moving each address over before each TMEM access
+  const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
   const int q = warp & 3, p = warp >> 2;
   const int r = 32 * q + lane;  // TMEM lane of this thread
   const int64_t t0 = (int64_t)blockIdx.y * kBT;
@@ -143,7 +156,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
-  const uint32_t tq = H.tbase + ((uint32_t)(32 * q) << 16);  // this quadrant's lanes, column 0
+  const uint32_t tq = __shfl_sync(0xffffffffu, H.tbase, 0) + ((uint32_t)(32 * q) << 16);  // quadrant's lanes, column 0
 
   // ------------------------------------------------ this warp's tile loads
   // Warp (q, p) writes the windows of channels c = p (mod 3) for quadrant q.
@@ -181,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   // (the window is then left unwritten and the block reports the error).
   auto write_window = [&](int c, int set) -> bool {
     const int m = (c - p) / kLead, j = m % kWS;
-    const int nch = (int)((uint32_t)__ldg(&gdesc[c].y) >> 24);
+    const int nch = __shfl_sync(0xffffffffu, (int)((uint32_t)__ldg(&gdesc[c].y) >> 24), 0);
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&H.sfull[warp][j], (uint32_t)((m / kWS) & 1), kWaitLimitCycles)))
       return false;
     const unsigned char* st = my_stages + (size_t)j * kStage;
@@ -235,17 +248,15 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   for (int jj = 0; jj < kTPW; ++jj)
 #pragma unroll
     for (int k = 0; k < 32; ++k) acc[jj][k] = 0.0f;
-  float X[kTPW * kPH], Y[kTPW * kPH];
+  float X[kPH], Y[kPH];
   uint32_t ta[kTPW];
   float wc = 1.0f;
   if constexpr (WEIGHTED) wc = __ldg(a.w);
   {
     const uint32_t cols = warp_cols(gdesc, p);
 #pragma unroll
-    for (int jj = 0; jj < kTPW; ++jj) {
-      ta[jj] = trial_addr(tq, cols, jj);
-      tmem_ld8(ta[jj], X + kPH * jj);
-    }
+    for (int jj = 0; jj < kTPW; ++jj) ta[jj] = trial_addr(tq, cols, jj);
+    tmem_ld16(ta[ph_trial(0)] + ph_col(0), X);
   }
   const int n_steps = (C + kLead - 1) / kLead;
 #pragma unroll 1
@@ -261,13 +272,12 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
       float wn = 1.0f;
       if constexpr (WEIGHTED) wn = more ? __ldg(a.w + c + 1) : wc;
 #pragma unroll
-      for (int ph = 0; ph < kNPH; ++ph) {
-        float* cur = (ph & 1) ? Y : X;
-        float* nxt = (ph & 1) ? X : Y;
-        tmem_wait_ld24(cur);
-        if (ph + 1 < kNPH) {
-#pragma unroll
-          for (int jj = 0; jj < kTPW; ++jj) tmem_ld8(ta[jj] + kPH * (ph + 1), nxt + kPH * jj);
+      for (int f = 0; f < kNPH; ++f) {
+        float* cur = (f & 1) ? Y : X;
+        float* nxt = (f & 1) ? X : Y;
+        tmem_wait_ld16(cur);
+        if (f + 1 < kNPH) {
+          tmem_ld16(ta[ph_trial(f + 1)] + ph_col(f + 1), nxt);
         } else if (more) {
           // the next channel; at a step boundary the next windows must be in
           // place and this step's slots free first
@@ -276,25 +286,24 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
           const int nk = k == kLead - 1 ? 0 : k + 1;
           const uint32_t slot_col = tq + (uint32_t)(kSlot * (kLead * nset + nk));
 #pragma unroll
-          for (int jj = 0; jj < kTPW; ++jj) {
-            ta[jj] = trial_addr(slot_col, cols_n, jj);
-            tmem_ld8(ta[jj], nxt + kPH * jj);
-          }
+          for (int jj = 0; jj < kTPW; ++jj) ta[jj] = trial_addr(slot_col, cols_n, jj);
+          tmem_ld16(ta[ph_trial(0)] + ph_col(0), nxt);
         }
-#pragma unroll
-        for (int jj = 0; jj < kTPW; ++jj) {
+        {
+          const int jj = ph_trial(f), c0 = ph_col(f);
 #pragma unroll
           for (int u = 0; u < kPH; u += 2) {
-            float& a0 = acc[jj][kPH * ph + u];
-            float& a1 = acc[jj][kPH * ph + u + 1];
+            float& a0 = acc[jj][c0 + u];
+            float& a1 = acc[jj][c0 + u + 1];
             if constexpr (WEIGHTED)
-              fma2_rn(a0, a1, wc, cur[kPH * jj + u], cur[kPH * jj + u + 1]);
+              fma2_rn(a0, a1, wc, cur[u], cur[u + 1]);
             else
-              add2_rn(a0, a1, cur[kPH * jj + u], cur[kPH * jj + u + 1]);
+              add2_rn(a0, a1, cur[u], cur[u + 1]);
           }
         }
-        // this warp's window of the next step, while a phase's loads are in flight
-        if (ph == 1 && k == p && ok) {
+        // this warp's window of the next step, while a phase's load is in
+        // flight (all warps at the same point of the step)
+        if (f == 1 && k == 1 && ok) {
           const int cw = kLead * (n + 1) + p;
           if (cw < C) ok = write_window(cw, set ^ 1);
         }
@@ -418,7 +427,8 @@ static bool encode_views(Tmw9Maps* maps, const FwdArgs& a) {
 
 cudaError_t launch_tmw9(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a, cudaStream_t s) {
   (void)cfg;
-  if (dtype != DD_F32_F32 || a.nine_desc == nullptr || !tmw9_accepts_avail(a.in, a.in_stride, a.in_avail, a.n_in))
+  if (dtype != DD_F32_F32) return cudaErrorInvalidConfiguration;
+  if (a.nine_desc == nullptr || !tmw9_accepts_avail(a.in, a.in_stride, a.in_avail, a.n_in))
     return cudaErrorInvalidConfiguration;
   Tmw9Maps maps;
   if (!encode_views(&maps, a)) return cudaErrorInvalidValue;

@@ -152,31 +152,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
       : "memory");
 }
 
-// Each thread loads 8 consecutive 32-bit columns of its own lane.  No memory
-// clobber: the load touches only Tensor Memory and the named registers.
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-               : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7])
-               : "r"(taddr));
+// Each thread loads 16 consecutive 32-bit columns of its own lane.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]), "=f"(v[7]), "=f"(v[8]),
+        "=f"(v[9]), "=f"(v[10]), "=f"(v[11]), "=f"(v[12]), "=f"(v[13]), "=f"(v[14]), "=f"(v[15])
+      : "r"(taddr));
 }
 
-// Wait for this thread's Tensor Memory loads, naming the 24 registers the
-// last loads wrote as operands, so that no use of them can be scheduled
+// Wait for this thread's Tensor Memory loads, naming the 16 registers the
+// last load wrote as operands, so that no use of them can be scheduled
 // before the wait.
-__device__ __forceinline__ void tmem_wait_ld24(float* v) {
+__device__ __forceinline__ void tmem_wait_ld16(float* v) {
   asm volatile("tcgen05.wait::ld.sync.aligned;"
                : "+f"(v[0]), "+f"(v[1]), "+f"(v[2]), "+f"(v[3]), "+f"(v[4]), "+f"(v[5]), "+f"(v[6]), "+f"(v[7]),
                  "+f"(v[8]), "+f"(v[9]), "+f"(v[10]), "+f"(v[11]), "+f"(v[12]), "+f"(v[13]), "+f"(v[14]),
-                 "+f"(v[15]), "+f"(v[16]), "+f"(v[17]), "+f"(v[18]), "+f"(v[19]), "+f"(v[20]), "+f"(v[21]),
-                 "+f"(v[22]), "+f"(v[23])
+                 "+f"(v[15])
                :
                : "memory");
-}
-
-// One 16-byte chunk of this thread's lane to 4 consecutive columns.
-__device__ __forceinline__ void tmem_st4(uint32_t taddr, float4 x) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1,%2,%3,%4};" ::"r"(taddr), "f"(x.x), "f"(x.y),
-               "f"(x.z), "f"(x.w));
 }
 
 // Four 16-byte chunks of this thread's lane to 16 consecutive columns.
