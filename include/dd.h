@@ -134,6 +134,17 @@ dd_status dd_plan_info(dd_plan_t plan, int64_t* n_in, int32_t* max_delay, int64_
  */
 dd_status dd_plan_in_stride(dd_plan_t plan, int64_t* in_row_stride);
 
+/*
+ * Host-only sizing (no device memory is touched): the device bytes that
+ * dd_plan of this geometry would hold (dd_plan_info's device_bytes of the
+ * plan it makes: the delay table of Eq. 1, its transposed copy, the status
+ * word and the window descriptors; n_out does not change it).  Arguments and
+ * errors as dd_plan.  For admission control, e.g. a serving loop that keeps
+ * beams within an HBM budget.
+ */
+dd_status dd_plan_footprint(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                            double dm_first, double dm_step, int32_t n_dm, dd_dtype dtype, int64_t* device_bytes);
+
 /* Copy the plan's delay table (Eq. 1, in samples) to host memory `host_out`,
  * row-major [n_dm][channels] int32.  For checking the plan against Eq. 1. */
 dd_status dd_plan_delays(dd_plan_t plan, int32_t* host_out);
@@ -345,6 +356,14 @@ dd_status dd_stream_create(dd_stream_t* out, dd_plan_t plan, int64_t chunk_len);
 dd_status dd_stream_push(dd_stream_t st, const void* chunk, void* out, int64_t* out_t0, void* stream);
 dd_status dd_stream_reset(dd_stream_t st, void* stream);
 dd_status dd_stream_state_bytes(dd_stream_t st, int64_t* bytes);
+/* Device bytes the stream holds: its own plan's tables (the geometry with
+ * n_out = chunk_len) and its two state buffers.  dd_stream_footprint reports
+ * the same number for a geometry before any stream exists (host-only;
+ * arguments and errors as dd_plan and dd_stream_create). */
+dd_status dd_stream_device_bytes(dd_stream_t st, int64_t* bytes);
+dd_status dd_stream_footprint(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                              double dm_first, double dm_step, int32_t n_dm, int64_t chunk_len, dd_dtype dtype,
+                              int64_t* device_bytes);
 dd_status dd_stream_save(dd_stream_t st, void* host_buf, void* stream);
 dd_status dd_stream_restore(dd_stream_t st, const void* host_buf, void* stream);
 dd_status dd_stream_destroy(dd_stream_t st);

@@ -87,6 +87,9 @@ def _declare(lib):
         "dd_stream_push": (st, [vp, vp, vp, P64, vp]),
         "dd_stream_reset": (st, [vp, vp]),
         "dd_stream_state_bytes": (st, [vp, P64]),
+        "dd_stream_device_bytes": (st, [vp, P64]),
+        "dd_plan_footprint": (st, [i32, dbl, dbl, dbl, dbl, dbl, i32, st, P64]),
+        "dd_stream_footprint": (st, [i32, dbl, dbl, dbl, dbl, dbl, i32, i64, st, P64]),
         "dd_stream_save": (st, [vp, vp, vp]),
         "dd_stream_restore": (st, [vp, vp, vp]),
         "dd_stream_destroy": (st, [vp]),
@@ -126,6 +129,23 @@ def delay_table(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n
     check(load().dd_delay_table_dm_range(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, dm_index0,
                                          n_dm, out.ctypes.data_as(ctypes.c_void_p)), "dd_delay_table_dm_range")
     return out
+
+
+def plan_footprint(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm, dtype="f32") -> int:
+    """Device bytes a plan of this geometry holds (dd_plan_footprint; host only)."""
+    n = ctypes.c_int64()
+    check(load().dd_plan_footprint(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm,
+                                   _DTYPES[dtype], ctypes.byref(n)), "dd_plan_footprint")
+    return n.value
+
+
+def stream_footprint(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm, chunk_len,
+                     dtype="f32") -> int:
+    """Device bytes a stream of this geometry holds (dd_stream_footprint; host only)."""
+    n = ctypes.c_int64()
+    check(load().dd_stream_footprint(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm,
+                                     int(chunk_len), _DTYPES[dtype], ctypes.byref(n)), "dd_stream_footprint")
+    return n.value
 
 
 def _rows(t, name, dtype, device):
@@ -404,6 +424,12 @@ class Stream:
     def state_bytes(self) -> int:
         n = ctypes.c_int64()
         check(load().dd_stream_state_bytes(self._h, ctypes.byref(n)), "dd_stream_state_bytes")
+        return n.value
+
+    def device_bytes(self) -> int:
+        """Device memory the stream holds (its plan's tables and two state buffers)."""
+        n = ctypes.c_int64()
+        check(load().dd_stream_device_bytes(self._h, ctypes.byref(n)), "dd_stream_device_bytes")
         return n.value
 
     def save(self, stream=None) -> bytes:

@@ -101,6 +101,9 @@ constexpr int kW9MaxOff = 31;
 // Input row stride (elements) that every forward configuration of a plan
 // takes: float rows with TMW9's spare samples, uint8 rows of 128 bytes.
 int64_t plan_in_stride(const dd_plan_s& p);
+// Device bytes of a stream's two state buffers [C][plan_in_stride] for its
+// chunk plan (the plan's geometry with n_out = chunk length).
+int64_t stream_buffer_bytes(const dd_plan_s& chunk_plan);
 
 }  // namespace dd
 

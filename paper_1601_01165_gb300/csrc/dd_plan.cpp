@@ -121,9 +121,36 @@ static int32_t build_nine_desc(const dd_plan_s& p, std::vector<int4>& desc) {
 
 int32_t block_spread_of(const dd_plan_s& p, int bd) { return block_spread(p, bd); }
 
+// Device memory of a plan's tables, from its host delay table alone: the
+// table [n_dm][C], its transposed padded copy [C][n_dm_pad], the status word,
+// and the 6- and 9-trial window descriptors where a group's offsets fit the
+// Tensor-Memory windows (float plans).  finish_plan allocates exactly these;
+// the footprint queries report the same numbers without allocating.
+struct TableSizes {
+  size_t delays = 0, delays_t = 0, status = sizeof(int), hex = 0, nine = 0;
+  int64_t total() const { return (int64_t)(delays + delays_t + status + hex + nine); }
+};
+static TableSizes table_sizes(const dd_plan_s& p) {
+  TableSizes t;
+  const int64_t n_dm_pad = (p.n_dm + kDmPad - 1) / kDmPad * kDmPad;
+  t.delays = (size_t)p.n_dm * p.C * 4;
+  t.delays_t = (size_t)p.C * n_dm_pad * 4;
+  if (p.dtype == DD_F32_F32) {
+    // a group's largest offset is its last trial's delay less its first's
+    if (block_spread(p, 6) <= kW6MaxOff) t.hex = (size_t)p.C * ((p.n_dm + 5) / 6) * sizeof(int4);
+    if (block_spread(p, 9) <= kW9MaxOff) t.nine = (size_t)p.C * ((p.n_dm + 8) / 9) * sizeof(int4);
+  }
+  return t;
+}
+
 int64_t plan_in_stride(const dd_plan_s& p) {
   if (p.dtype == DD_U8_I32) return (p.n_in + 127) / 128 * 128;
   return tmw9_min_in_stride(p.n_in);
+}
+
+int64_t stream_buffer_bytes(const dd_plan_s& chunk_plan) {
+  const int64_t elem = chunk_plan.dtype == DD_U8_I32 ? 1 : 4;
+  return 2 * (int64_t)chunk_plan.C * plan_in_stride(chunk_plan) * elem;
 }
 
 void free_plan_device(dd_plan_s* p) {
@@ -200,7 +227,8 @@ dd_status finish_plan(dd_plan_s* p) {
   for (int32_t c = 0; c < p->C; ++c)
     for (int32_t i = 0; i < p->n_dm_pad; ++i)
       dT[(size_t)c * p->n_dm_pad + i] = p->delays[(size_t)std::min(i, p->n_dm - 1) * p->C + c];
-  const size_t bytes_d = p->delays.size() * 4, bytes_dT = dT.size() * 4;
+  const TableSizes sizes = table_sizes(*p);
+  const size_t bytes_d = sizes.delays, bytes_dT = sizes.delays_t;
   cudaError_t e = cudaMalloc(&p->d_delays, bytes_d);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_delaysT, bytes_dT);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_status, sizeof(int));
@@ -215,7 +243,7 @@ dd_status finish_plan(dd_plan_s* p) {
   p->device_bytes = (int64_t)(bytes_d + bytes_dT + sizeof(int));
   // 6-trial descriptors, only where the windows fit (float plans, offsets <= 31)
   bool hex_ok = false;
-  if (p->dtype == DD_F32_F32) {
+  if (sizes.hex > 0) {
     std::vector<int4> desc6;
     if (build_hex_desc(*p, desc6) <= kW6MaxOff) {
       const size_t bytes6 = desc6.size() * sizeof(int4);
@@ -231,7 +259,7 @@ dd_status finish_plan(dd_plan_s* p) {
     }
   }
   bool nine_ok = false;
-  if (p->dtype == DD_F32_F32) {
+  if (sizes.nine > 0) {
     std::vector<int4> desc9;
     if (build_nine_desc(*p, desc9) <= kW9MaxOff) {
       const size_t bytes9 = desc9.size() * sizeof(int4);
@@ -379,6 +407,54 @@ extern "C" dd_status dd_plan_dm_range(dd_plan_t* out, int32_t channels, double f
   }
   apply_tune_db(p);
   *out = p;
+  return DD_OK;
+}
+
+// A host-only plan of the given geometry with its delay table (no device
+// memory), for the footprint queries.
+static dd_status host_plan(dd_plan_s& p, int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                           double dm_first, double dm_step, int32_t n_dm, int64_t n_out, dd_dtype dtype) {
+  dd_status st = check_plan_args(channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm);
+  if (st != DD_OK) return st;
+  if (dtype != DD_U8_I32 && dtype != DD_F32_F32) return set_error(DD_ERR_ARG, "unknown dtype %d", (int)dtype);
+  p.C = channels;
+  p.n_dm = n_dm;
+  p.n_out = n_out;
+  p.f_low = f_low_mhz;
+  p.chan_bw = chan_bw_mhz;
+  p.t_samp = t_samp_s;
+  p.dm_first = dm_first;
+  p.dm_step = dm_step;
+  p.dtype = dtype;
+  st = compute_delay_table(p);
+  if (st != DD_OK) return st;
+  p.max_delay = *std::max_element(p.delays.begin(), p.delays.end());
+  p.n_in = p.n_out + p.max_delay;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_plan_footprint(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                                       double dm_first, double dm_step, int32_t n_dm, dd_dtype dtype,
+                                       int64_t* device_bytes) {
+  clear_error();
+  if (!device_bytes) return set_error(DD_ERR_ARG, "dd_plan_footprint: device_bytes is NULL");
+  dd_plan_s p;
+  dd_status st = host_plan(p, channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm, 1, dtype);
+  if (st != DD_OK) return st;
+  *device_bytes = table_sizes(p).total();
+  return DD_OK;
+}
+
+extern "C" dd_status dd_stream_footprint(int32_t channels, double f_low_mhz, double chan_bw_mhz, double t_samp_s,
+                                         double dm_first, double dm_step, int32_t n_dm, int64_t chunk_len,
+                                         dd_dtype dtype, int64_t* device_bytes) {
+  clear_error();
+  if (!device_bytes) return set_error(DD_ERR_ARG, "dd_stream_footprint: device_bytes is NULL");
+  if (chunk_len <= 0) return set_error(DD_ERR_ARG, "dd_stream_footprint: chunk_len must be > 0");
+  dd_plan_s p;  // the stream's own plan: the same geometry, n_out = chunk_len
+  dd_status st = host_plan(p, channels, f_low_mhz, chan_bw_mhz, t_samp_s, dm_first, dm_step, n_dm, chunk_len, dtype);
+  if (st != DD_OK) return st;
+  *device_bytes = table_sizes(p).total() + stream_buffer_bytes(p);
   return DD_OK;
 }
 

@@ -57,7 +57,7 @@ extern "C" dd_status dd_stream_create(dd_stream_t* out, dd_plan_t plan, int64_t 
   st->elem = plan->dtype == DD_U8_I32 ? 1 : 4;
   // rows padded so that every configuration of the chunk plan takes the buffer
   st->stride = plan_in_stride(*st->chunk_plan);
-  const size_t bytes = (size_t)st->C * st->stride * st->elem;
+  const size_t bytes = (size_t)stream_buffer_bytes(*st->chunk_plan) / 2;
   cudaError_t e = cudaMalloc(&st->buf[0], bytes);
   if (e == cudaSuccess) e = cudaMalloc(&st->buf[1], bytes);
   if (e == cudaSuccess) e = cudaMemset(st->buf[0], 0, bytes);
@@ -106,6 +106,13 @@ extern "C" dd_status dd_stream_reset(dd_stream_t st, void* stream) {
   if (e != cudaSuccess) return set_cuda_error("dd_stream_reset", e);
   st->cur = 0;
   st->pushed = 0;
+  return DD_OK;
+}
+
+extern "C" dd_status dd_stream_device_bytes(dd_stream_t st, int64_t* bytes) {
+  clear_error();
+  if (!st || !bytes) return set_error(DD_ERR_ARG, "dd_stream_device_bytes: NULL argument");
+  *bytes = st->chunk_plan->device_bytes + stream_buffer_bytes(*st->chunk_plan);
   return DD_OK;
 }
 

@@ -80,19 +80,17 @@ class _Active:
 
 
 def beam_bytes(spec: BeamSpec) -> int:
-    """Device memory a running beam holds (tables, two tail buffers, one chunk in, one chunk out)."""
+    """Device memory a running beam holds, as the library reports it before
+    anything is allocated: the beam's plan (dd_plan_footprint), its stream
+    (dd_stream_footprint: the stream's own plan and its two state buffers
+    with the max-delay tail) and the server's chunk buffers (one input chunk,
+    one output chunk)."""
     s = spec.setup
+    geo = (s.channels, s.f_low_mhz, s.chan_bw_mhz, s.t_samp_s, s.dm_first, s.dm_step, s.n_dm)
     elem = 1 if spec.dtype == "u8" else 4
-    d = binding.delay_table(s.channels, s.f_low_mhz, s.chan_bw_mhz, s.t_samp_s, s.dm_first, s.dm_step, s.n_dm)
-    max_d = int(d.max())
-    v = 128 // elem                                   # tail buffers use 128-byte rows
-    stride = (max_d + spec.chunk_len + v - 1) // v * v
-    n_dm_pad = (s.n_dm + 63) // 64 * 64
-    tables = 4 * s.channels * (s.n_dm + n_dm_pad)     # delay table and its transposed copy
-    if spec.dtype == "f32":                           # 6-trial window descriptors (at most)
-        tables += 16 * s.channels * ((s.n_dm + 5) // 6)
-    return int(2 * s.channels * stride * elem + s.channels * spec.chunk_len * elem +
-               4 * s.n_dm * spec.chunk_len + tables)
+    chunks = s.channels * spec.chunk_len * elem + 4 * s.n_dm * spec.chunk_len
+    return (binding.plan_footprint(*geo, dtype=spec.dtype) +
+            binding.stream_footprint(*geo, spec.chunk_len, dtype=spec.dtype) + chunks)
 
 
 class AdmissionError(RuntimeError):
