@@ -38,8 +38,11 @@ from paper_1601_01165_gb300 import synth  # noqa: E402
 METRIC = "dedispersed DM-trial·samples/s and achieved HBM GB/s (fraction of roofline), 1 GB300"
 UNIT = "DM-trial·samples/s"
 L2_BYTES = 129 * 1024 * 1024
-SMS = 152
 FP32_LANES_PER_SM = 128
+# int32 lanes per SM: 128 on the integer (ALU) pipe plus 128 on the FMA pipe,
+# which also runs integer multiply-adds (a probe measured 251 int32 adds per
+# clock per SM); the uint8 path's roof counts one int32 add per 8-bit add
+INT32_LANES_PER_SM = 256
 SM_MAX_MHZ_NOMINAL = 2070.0
 
 # DRAM traffic per launch from ncu (dram__bytes_read.sum + dram__bytes_write.sum),
@@ -285,6 +288,217 @@ def _config(setup, args, cfg_name, l2_note):
             "parallelism": f"beams: one per GPU x {args.gpus}"}
 
 
+def _sm_count(dev) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
+
+
+def _rotating_inputs(plan, setup, dtype, dev, seed, make_host=None):
+    """Input buffers of the plan's padded stride, enough of them that the
+    bytes rotated through exceed twice the L2 (so every launch reads cold)."""
+    import torch
+    d = plan.delays()
+    stride = plan.padded_in_stride()
+    elem = 1 if dtype == "u8" else 4
+    in_bytes = setup.channels * stride * elem
+    n_buf = max(2, int(np.ceil(2 * L2_BYTES / in_bytes)) + 1)
+    host_x, _ = _make_input(setup, dtype, seed, plan.n_in, stride, d)
+    xs = [torch.from_numpy(host_x).to(dev) for _ in range(n_buf)]
+    return host_x, xs, n_buf, in_bytes
+
+
+def _time_launches(fn, n_buf, steps, warmup, stream):
+    """Warm-up, then `steps` launches bracketed by CUDA events on `stream`;
+    returns the per-launch times (ms) and the total (ms)."""
+    import torch
+    for k in range(warmup):
+        fn(k % n_buf)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    ev[0].record(stream)
+    for k in range(steps):
+        fn(k % n_buf)
+        ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)], ev[0].elapsed_time(ev[steps])
+
+
+def _roofline(setup, plan, dtype, avg_ms, sms, sm_max, peak_kind, hbm_gbs, cfg_name):
+    """The dominant kernel against the add roof (float: FP32 lanes; uint8:
+    int32 lanes), with the HBM fraction of its compulsory bytes beside it."""
+    elem = 1 if dtype == "u8" else 4
+    adds = setup.adds
+    compulsory = setup.channels * plan.n_in * elem + setup.n_dm * setup.n_out * 4 + 4 * setup.n_dm * setup.channels
+    lanes = INT32_LANES_PER_SM if dtype == "u8" else FP32_LANES_PER_SM
+    add_peak = sms * lanes * sm_max * 1e6 / 1e12      # T adds/s
+    achieved_alu = adds / (avg_ms / 1e3) / 1e12
+    achieved_hbm = compulsory / (avg_ms / 1e3) / 1e9
+    kh = _kernel_hash()
+    tr = NCU_TRAFFIC.get((setup.name, setup.n_out, cfg_name, dtype))
+    traffic = tr["bytes"] if tr and tr.get("hash") == kh else None
+    lane_note = (f"{lanes} int32 lanes (128 ALU + 128 FMA pipe), one int32 add per 8-bit add" if dtype == "u8"
+                 else f"{lanes} FP32 lanes, 1 add = 1 op (Eq. 2 counts one add per input sample)")
+    return {"bound": "alu", "achieved": achieved_alu, "peak": add_peak,
+            "unit": "TFLOP/s" if dtype == "f32" else "Tops", "frac": achieved_alu / add_peak,
+            "traffic": traffic,
+            "peak_note": f"{sms} SMs x {lane_note}, {sm_max:.0f} MHz ({peak_kind} max clock)",
+            "per_launch_ops": adds, "avg_launch_ms": avg_ms,
+            "hbm": {"achieved_gbs": achieved_hbm, "peak_gbs": hbm_gbs, "frac": achieved_hbm / hbm_gbs,
+                    "compulsory_bytes": compulsory, "peak_kind": peak_kind,
+                    "ncu_traffic_gbs": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9,
+                    "ncu_traffic_frac": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9 / hbm_gbs},
+            # Eq. 2's accounting: every add reads its own input sample (no reuse);
+            # an effective rate for comparison with the paper's figures, not bytes moved
+            "eq2_effective_gbs": elem * adds / (avg_ms / 1e3) / 1e9}
+
+
+def _extra_config(setup, dtype, steps, warmup, dev, sms, sm_max, peak_kind, hbm_gbs):
+    """One more configuration timed like the headline (cold L2, CUDA events)."""
+    import torch
+    from paper_1601_01165_gb300 import binding as dd
+    plan = dd.Plan.from_setup(setup, dtype)
+    _, xs, n_buf, in_bytes = _rotating_inputs(plan, setup, dtype, dev, 0)
+    out = torch.empty((setup.n_dm, setup.n_out), dtype=plan.out_dtype, device=dev)
+    stream = torch.cuda.current_stream()
+    launch_ms, total_ms = _time_launches(lambda k: plan.forward(xs[k], out=out), n_buf, steps, warmup, stream)
+    if plan.device_status() != 0:
+        raise RuntimeError(f"device status nonzero ({setup.name} {dtype})")
+    avg = statistics.fmean(launch_ms)
+    res = {"workload": f"{setup.name}-like beam, {setup.channels} ch, {setup.n_dm} DM trials, {setup.n_out} samples",
+           "dtype": dtype, "kernel_config": plan.selected, "value": setup.n_dm * setup.n_out / (total_ms / steps / 1e3),
+           "unit": UNIT, "ms_per_step": total_ms / steps, "steps": steps,
+           "l2": f"{n_buf} rotating input buffers ({n_buf * in_bytes / 2**20:.0f} MiB > 2x L2)",
+           "roofline": _roofline(setup, plan, dtype, avg, sms, sm_max, peak_kind, hbm_gbs, plan.selected)}
+    del xs, out
+    plan.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def _streamed_vs_plain(steps, warmup, dev):
+    """Section 4.2's real-time form on the Apertif-like uint8 beam: 1 s chunks
+    through dd_stream_push (the max-delay tail stays on the device; only the
+    new second is sent) against the plain per-beam launch of the same second
+    (dd_forward over n_out = 1 s, whose input must carry the tail again).
+    Timed on the device (inputs resident, rotating > 2x L2) and end to end
+    from pinned host memory (chunk in, result out, copies timed)."""
+    import torch
+    from paper_1601_01165_gb300 import binding as dd
+    s = synth.APERTIF
+    n = s.n_out
+    plan = dd.Plan.from_setup(s, "u8")
+    st = dd.Stream(plan, n)
+    chunk_bytes = s.channels * n
+    n_chunks = max(2, int(np.ceil(2 * L2_BYTES / chunk_bytes)) + 1)
+    chunks = [torch.from_numpy(synth.noise_u8(100 + k, s.channels, n)).to(dev) for k in range(n_chunks)]
+    out_s = torch.empty((s.n_dm, n), dtype=torch.int32, device=dev)
+    _, xs, n_buf, in_bytes = _rotating_inputs(plan, s, "u8", dev, 1)
+    out_p = torch.empty((s.n_dm, n), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream()
+    k_steps = max(5, min(steps, 20))
+    st_ms, st_total = _time_launches(lambda k: st.push(chunks[k], out=out_s), n_chunks, k_steps, warmup, stream)
+    pl_ms, pl_total = _time_launches(lambda k: plan.forward(xs[k], out=out_p), n_buf, k_steps, warmup, stream)
+    # end to end over consecutive seconds from pinned host memory (chunk in,
+    # result out, the same output bytes both ways).  The streamed form runs
+    # as a real-time pipeline does: second k + 1 is copied in while second k
+    # is dedispersed and second k - 1 copied out (a copy-in stream, the push
+    # stream, two copy-out streams; two buffers each; the pushes stay in order
+    # on one stream).  The plain form calls
+    # dd_forward_host once per second (it pipelines time chunks inside the
+    # call and returns with the result in host memory).
+    h_chunk = torch.from_numpy(synth.noise_u8(7, s.channels, n)).pin_memory()
+    h_beam = torch.from_numpy(np.ascontiguousarray(synth.noise_u8(7, s.channels, plan.n_in))).pin_memory()
+    h_outs = [torch.empty((s.n_dm, n), dtype=torch.int32, pin_memory=True) for _ in range(2)]
+    d_chunks = [torch.empty((s.channels, n), dtype=torch.uint8, device=dev) for _ in range(2)]
+    d_outs = [out_s, torch.empty((s.n_dm, n), dtype=torch.int32, device=dev)]
+    s_in, s_run = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    s_outs = [torch.cuda.Stream(device=dev) for _ in range(2)]   # copy-outs alternate, as in dd_forward_host
+    ev_in = [torch.cuda.Event() for _ in range(2)]
+    ev_run = [torch.cuda.Event() for _ in range(2)]
+    ev_out = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_stream(seconds):
+        for k in range(seconds):
+            b = k & 1
+            if k >= 2:
+                s_in.wait_event(ev_run[b])      # the push of second k - 2 has read this chunk buffer
+            with torch.cuda.stream(s_in):
+                d_chunks[b].copy_(h_chunk, non_blocking=True)
+                ev_in[b].record(s_in)
+            s_run.wait_event(ev_in[b])
+            if k >= 2:
+                s_run.wait_event(ev_out[b])     # second k - 2's result has left this output buffer
+            st.push(d_chunks[b], out=d_outs[b], stream=s_run)
+            ev_run[b].record(s_run)
+            s_out = s_outs[b]
+            s_out.wait_event(ev_run[b])
+            with torch.cuda.stream(s_out):
+                h_outs[b].copy_(d_outs[b], non_blocking=True)
+                ev_out[b].record(s_out)
+        for so in s_outs:
+            so.synchronize()
+
+    def e2e_plain(seconds):
+        for _ in range(seconds):
+            plan.forward_host(h_beam, out=h_outs[0])
+
+    def wall(fn):
+        fn(2)
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        fn(k_steps)
+        return (time.perf_counter() - t) / k_steps * 1e3
+
+    e2e_s, e2e_p = wall(e2e_stream), wall(e2e_plain)
+    units = s.n_dm * n
+    res = {"workload": f"apertif-like uint8 beam, 1 s chunks of {n} samples, {s.n_dm} DM trials",
+           "streamed_ms_per_chunk": st_total / k_steps, "plain_ms_per_second": pl_total / k_steps,
+           "streamed_value": units / (st_total / k_steps / 1e3), "plain_value": units / (pl_total / k_steps / 1e3),
+           "device_speedup_streamed_vs_plain": pl_total / st_total,
+           "e2e_streamed_ms": e2e_s, "e2e_plain_ms": e2e_p, "e2e_speedup_streamed_vs_plain": e2e_p / e2e_s,
+           "h2d_bytes_streamed": chunk_bytes, "h2d_bytes_plain": s.channels * plan.n_in,
+           "note": "the streamed form sends only the new second and pipelines consecutive seconds; the plain "
+                   "launch re-sends the max-delay overlap with every second (Section 2.1: n_in = n_out + "
+                   "max_delay) and returns with each second's result; on the device alone both run the "
+                   "same kernel (the stream adds two device copies: chunk behind the tail, new tail)",
+           "unit": UNIT, "steps": k_steps}
+    st.close()
+    plan.close()
+    torch.cuda.empty_cache()
+    return res
+
+
+def _serving_summary(beams, chunks, seed, kernel_ms_u8):
+    """A short real-time serving run (Section 4.2 / 5.1): Apertif-like uint8
+    beams delivering 1 s chunks on their own timers, continuous batching with
+    HBM-budget admission; plus the beams-in-real-time count implied by the
+    kernel time of one beam-second."""
+    from paper_1601_01165_gb300.serve import BeamSpec, Server, beam_bytes
+    base = synth.APERTIF
+    rng = np.random.default_rng(seed)
+    specs = [BeamSpec(f"beam{b}", base, "u8", chunk_len=base.n_out, n_chunks=chunks,
+                      period_s=base.n_out * base.t_samp_s, phase_s=float(rng.uniform(0, 1)))
+             for b in range(beams)]
+    cache = {}
+
+    def source(sp, k):
+        key = k % 4
+        if key not in cache:
+            cache[key] = synth.noise_u8(seed + key, base.channels, base.n_out)
+        return cache[key]
+
+    budget = beams * beam_bytes(specs[0]) + 1
+    rep = Server(budget).run(specs, source)
+    return {"workload": f"{beams} apertif-like uint8 beams x {chunks} chunks of 1 s, random phases, "
+                        f"HBM budget {budget / 2**30:.1f} GiB",
+            "chunks": rep["chunks"], "latency_p50_s": rep["latency_p50_s"], "latency_p99_s": rep["latency_p99_s"],
+            "latency_max_s": rep["latency_max_s"], "deadline_s": specs[0].period_s,
+            "deadline_misses": rep["deadline_misses"], "peak_beams": rep["peak_beams"],
+            "beams_realtime_kernel_bound": int(1000.0 / kernel_ms_u8) if kernel_ms_u8 else None,
+            "beams_realtime_note": "one beam-second is one forward over 20,000 samples; the kernel-bound count is "
+                                   "1 s / that kernel time (the paper's Section 5.1 sizing: 9 beams per HD7970)"}
+
+
 def run_ours(args, setup):
     import torch
     ws, rank, local = _dist()
@@ -301,13 +515,8 @@ def run_ours(args, setup):
     if args.config:
         plan.select(args.config)
     cfg_name = plan.selected
-    d = plan.delays()
-    stride = plan.padded_in_stride()
     elem = 1 if args.dtype == "u8" else 4
-    in_bytes = setup.channels * stride * elem
-    n_buf = max(2, int(np.ceil(2 * L2_BYTES / in_bytes)) + 1)
-    host_x, _ = _make_input(setup, args.dtype, rank, plan.n_in, stride, d)
-    xs = [torch.from_numpy(host_x).to(dev) for _ in range(n_buf)]
+    host_x, xs, n_buf, in_bytes = _rotating_inputs(plan, setup, args.dtype, dev, rank)
     out = torch.empty((setup.n_dm, setup.n_out), dtype=plan.out_dtype, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -385,28 +594,9 @@ def run_ours(args, setup):
         return 0
 
     hbm_gbs, sm_max, peak_kind = _peaks()
+    sms = _sm_count(dev)
     avg_ms = statistics.fmean(launch_ms)
-    adds = setup.adds
-    compulsory = setup.channels * plan.n_in * elem + setup.n_dm * setup.n_out * 4 + 4 * setup.n_dm * setup.channels
-    add_peak = SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12      # T adds/s
-    achieved_alu = adds / (avg_ms / 1e3) / 1e12
-    achieved_hbm = compulsory / (avg_ms / 1e3) / 1e9
-    kh = _kernel_hash()
-    tr = NCU_TRAFFIC.get((setup.name, setup.n_out, cfg_name, args.dtype))
-    traffic = tr["bytes"] if tr and tr.get("hash") == kh else None
-    roof = {"bound": "alu", "achieved": achieved_alu, "peak": add_peak,
-            "unit": "TFLOP/s" if args.dtype == "f32" else "Tops", "frac": achieved_alu / add_peak,
-            "traffic": traffic,
-            "peak_note": f"{SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_max:.0f} MHz ({peak_kind} max clock), "
-                         f"1 add = 1 op (Eq. 2 counts one add per input sample)",
-            "per_launch_ops": adds, "avg_launch_ms": avg_ms,
-            "hbm": {"achieved_gbs": achieved_hbm, "peak_gbs": hbm_gbs, "frac": achieved_hbm / hbm_gbs,
-                    "compulsory_bytes": compulsory, "peak_kind": peak_kind,
-                    "ncu_traffic_gbs": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9,
-                    "ncu_traffic_frac": None if traffic is None else traffic / (avg_ms / 1e3) / 1e9 / hbm_gbs},
-            # Eq. 2's accounting: every add reads its own 4-byte sample (no reuse); an
-            # effective rate for comparison with the paper's figures, not bytes moved
-            "eq2_effective_gbs": 4.0 * adds / (avg_ms / 1e3) / 1e9}
+    roof = _roofline(setup, plan, args.dtype, avg_ms, sms, sm_max, peak_kind, hbm_gbs, cfg_name)
     clocks = sampler.summary()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -415,10 +605,25 @@ def run_ours(args, setup):
         "config": _config(setup, args, cfg_name,
                           f"{n_buf} rotating input buffers ({n_buf * in_bytes / 2**20:.0f} MiB > 2x L2)"),
         "roofline": roof, "e2e": e2e, "gpu_launches": args.steps, "clocks": clocks,
-        "kernel_source_hash": kh,
+        "kernel_source_hash": _kernel_hash(),
         "launch_ms": {"min": min(launch_ms), "p10": _pct(launch_ms, 10), "median": statistics.median(launch_ms),
                       "p90": _pct(launch_ms, 90), "max": max(launch_ms), "warm_l2_mean": warm_ms},
     }
+    del xs, out
+    plan.close()
+    torch.cuda.empty_cache()
+    # the other configurations of the headline metric, timed the same way (default run only)
+    if ws == 1 and not args.no_extra and args.n_out is None and args.workload == "apertif" and \
+            args.dtype == "f32" and not args.config:
+        ke = max(5, min(args.steps, 20))
+        extra = {"apertif_u8": _extra_config(synth.APERTIF, "u8", ke, args.warmup, dev, sms, sm_max, peak_kind,
+                                             hbm_gbs),
+                 "lofar_f32": _extra_config(synth.LOFAR, "f32", ke, args.warmup, dev, sms, sm_max, peak_kind,
+                                            hbm_gbs)}
+        extra["streamed_vs_plain_u8"] = _streamed_vs_plain(ke, args.warmup, dev)
+        extra["serving_u8"] = _serving_summary(args.serve_beams, 2, args.seed,
+                                               extra["apertif_u8"]["ms_per_step"])
+        line["extra"] = extra
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(setup, args.dtype)
         line["cpu_baseline_parallel"] = cpu_baseline_parallel(setup, args.dtype)
@@ -570,13 +775,15 @@ def run_dm_sweep(args):
     2, 4, ..., 4096 trials on the Apertif grid, and for perfect data reuse
     (dm_step = 0, every delay zero, Section 4.2), time every configuration of
     the plan, keep the fastest, and compare it with the generic one-trial-per-
-    thread kernel (Section 5's "generic" code).  Prints the table and the
-    histogram of tuned configurations."""
+    thread kernel (Section 5's "generic" code).  Fig. 3's analogue: for every
+    case, the distribution of throughput over all configurations timed (a
+    histogram of GFLOP/s, one add = one floating-point operation as the paper
+    counts), with the tuned and generic values and their ratio."""
     import tempfile
     import torch
     from paper_1601_01165_gb300 import binding as dd
     torch.cuda.set_device(0)
-    rows, hist = [], {}
+    rows, winners, hists = [], {}, {}
     cases = [(n, synth.APERTIF.dm_step) for n in [2 ** k for k in range(1, 13)]] + [(2048, 0.0)]
     with tempfile.TemporaryDirectory() as tmp:
         for dtype in ("f32", "u8"):
@@ -589,7 +796,17 @@ def run_dm_sweep(args):
                     timings = json.loads(f.readline())["timings"]
                 generic = min(v for k, v in timings.items() if k.startswith("naive"))
                 fam = name.split("_")[0]
-                hist[f"{dtype}:{fam}"] = hist.get(f"{dtype}:{fam}", 0) + 1
+                winners[f"{dtype}:{fam}"] = winners.get(f"{dtype}:{fam}", 0) + 1
+                gflops = {k: s.adds / (v / 1e3) / 1e9 for k, v in timings.items()}
+                vals = np.array(sorted(gflops.values()))
+                edges = np.linspace(vals[0], vals[-1], 9) if vals[-1] > vals[0] else np.array([vals[0], vals[0] + 1])
+                counts, _ = np.histogram(vals, edges)
+                key = f"{dtype}:{n_dm}" + (":perfect-reuse" if step == 0.0 else "")
+                hists[key] = {"gflops_bin_edges": [round(float(e), 1) for e in edges],
+                              "configs_per_bin": [int(c) for c in counts],
+                              "configs": int(len(vals)), "median_gflops": float(np.median(vals)),
+                              "tuned_gflops": float(vals[-1]), "generic_gflops": s.adds / (generic / 1e3) / 1e9,
+                              "tuned_over_generic": generic / ms, "tuned_config": name}
                 rows.append({"dtype": dtype, "n_dm": n_dm, "dm_step": step, "tuned": name, "tuned_ms": ms,
                              "generic_ms": generic, "speedup_vs_generic": generic / ms,
                              "dm_samples_per_s": n_dm * s.n_out / (ms / 1e3), "configs_timed": len(timings)})
@@ -598,10 +815,11 @@ def run_dm_sweep(args):
     units = sum(r["n_dm"] * synth.APERTIF.n_out for r in rows)
     total_ms = sum(r["tuned_ms"] for r in rows)
     line = {"metric": METRIC, "workload": "dm-sweep", "value": units / (total_ms / 1e3), "unit": UNIT,
-            "n_gpus": 1, "higher_is_better": True, "rows": rows, "histogram": hist,
+            "n_gpus": 1, "higher_is_better": True, "rows": rows, "histogram": hists, "winning_families": winners,
             "config": {"workload": "Apertif grid (1024 ch, 20000 samples), 2..4096 DM trials step 0.25, "
                                    "plus 2048 trials at dm_step 0; float32 and uint8; every configuration timed "
-                                   "(median of 5 after 2 warm-ups, warm L2)"}}
+                                   "(median of 5 after 2 warm-ups, warm L2); histogram: GFLOP/s over the "
+                                   "configurations of each case, 8 equal bins from slowest to fastest"}}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -663,6 +881,9 @@ def main():
                     help="output samples per beam instead of the setup's (smaller cases for profiling)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="default run: skip the uint8, LOFAR, streamed and serving lines beside the headline")
+    ap.add_argument("--serve-beams", type=int, default=40, help="beams of the default run's short serving line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

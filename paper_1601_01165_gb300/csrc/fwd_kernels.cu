@@ -666,8 +666,11 @@ cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs&
 std::vector<TileConfig> staged_menu(dd_dtype dtype) {
   std::vector<TileConfig> v;
   (void)dtype;
+  // the generic kernel's block size is a launch parameter: four shapes
   v.push_back({Kind::Naive, 1, 256, 0, 0, 256, 0, 0, 0, "naive_t256"});
   v.push_back({Kind::Naive, 1, 128, 0, 0, 128, 0, 0, 0, "naive_t128"});
+  v.push_back({Kind::Naive, 1, 64, 0, 0, 64, 0, 0, 0, "naive_t64"});
+  v.push_back({Kind::Naive, 1, 32, 0, 0, 32, 0, 0, 0, "naive_t32"});
 #define X(BD_, BT_, CC_, ST_)                                                            \
   v.push_back({Kind::Staged, BD_, BT_, CC_, ST_, 256, 0, 0, 0,                           \
                "staged_d" #BD_ "_t" #BT_ "_c" #CC_ "_s" #ST_});

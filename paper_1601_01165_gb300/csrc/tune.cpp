@@ -89,8 +89,9 @@ extern "C" dd_status dd_tune(dd_plan_t plan, double budget_s, const char* db_pat
     }
   }
   const int elem = plan->dtype == DD_U8_I32 ? 1 : 4;
-  const int64_t v = 128 / elem;  // 128-byte rows: every configuration takes the input
-  const int64_t stride = (plan->n_in + v - 1) / v * v;
+  // the stride every configuration takes as it is (no launch falls back to
+  // another configuration, so each timing is the named configuration's)
+  const int64_t stride = plan_in_stride(*plan);
   void* in = nullptr;
   void* out = nullptr;
   cudaStream_t s = nullptr;

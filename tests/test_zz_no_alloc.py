@@ -71,10 +71,13 @@ def test_noalloc_matches_allocating_entry_point_twice(lib):
 
 def test_noalloc_accepts_the_maximum_row_count(lib):
     # exactly DD_NOALLOC_MAX_ROWS rows fill the whole fixed scratch; the
-    # maximum sits in the last row, whose scratch entry is the array's last
+    # maximum sits in the last row, whose scratch entry is the array's last.
+    # S/N is measured against each row's own spread, which a pulse widens, so
+    # the pulse must be a small part of its row to stand out: with 512 columns
+    # its S/N (about 9) is far above the best noise row's (about 5)
     g = torch.Generator(device="cpu").manual_seed(3)
-    x = torch.randn((MAX_ROWS, 16), generator=g)
-    x[MAX_ROWS - 1, 4:12] += 9.0
+    x = torch.randn((MAX_ROWS, 512), generator=g)
+    x[MAX_ROWS - 1, 200:208] += 9.0
     x = x.cuda()
     ref_raw, ref_grad = _call(lib, "dd_boxcar_snr", x)
     got_raw, got_grad = _call(lib, "dd_boxcar_snr_noalloc", x)
