@@ -635,7 +635,11 @@ def run_ours(args, setup):
 
 
 def run_batched(args):
-    """64 uneven beams: one CUDA-graph launch of every beam's forward vs 64 plain launches of the same plans."""
+    """64 uneven beams (Section 5.1: many beams per device): the batch (one
+    CUDA-graph launch of every beam's forward, beams dealt to internal streams
+    longest first) against 64 plain launches of the same plans, first with each
+    plan's default configuration, then after dd_batch_tune has tuned each
+    distinct setup once (both forms then run the tuned kernels)."""
     import torch
     from paper_1601_01165_gb300 import binding as dd
     torch.cuda.set_device(0)
@@ -677,8 +681,21 @@ def run_batched(args):
         for p, x, o in zip(plans, xs, outs):
             p.forward(x, out=o, stream=stream)
 
+    def solo_sum():
+        """Sum of each beam's own launch time (each timed alone)."""
+        tot = 0.0
+        for p, x, o in zip(plans, xs, outs):
+            tot += timed(lambda: p.forward(x, out=o, stream=stream), 3)
+        return tot
+
+    ms_batch_def = timed(run_batch, args.steps)
+    ms_plain_def = timed(run_plain, args.steps)
+    t0 = time.perf_counter()
+    n_setups = batch.tune(budget_s=args.tune_budget)
+    tune_s = time.perf_counter() - t0
     ms_batch = timed(run_batch, args.steps)
     ms_plain = timed(run_plain, args.steps)
+    ms_solo = solo_sum()
     # the batch's results equal the per-beam launches (checked on every beam)
     with torch.cuda.stream(stream):
         run_batch()
@@ -687,10 +704,15 @@ def run_batched(args):
     same = all(torch.equal(o, r) for o, r in zip(outs, ref))
     line = {"metric": METRIC, "workload": "batched", "value": units / (ms_batch / 1e3), "unit": UNIT,
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
-            "plain_launches_ms": ms_plain, "speedup_vs_plain": ms_plain / ms_batch, "beams": len(beams),
-            "adds_per_step": adds, "batch_equals_plain": same, "gpu_launches": 2 * args.steps,
+            "plain_launches_ms": ms_plain, "speedup_vs_plain": ms_plain / ms_batch,
+            "default_configs": {"batch_ms": ms_batch_def, "plain_launches_ms": ms_plain_def,
+                                "speedup_vs_plain": ms_plain_def / ms_batch_def},
+            "tuned_over_default_batch": ms_batch_def / ms_batch, "setups_tuned": n_setups, "tune_s": tune_s,
+            "sum_of_solo_launch_ms": ms_solo, "batch_over_solo_sum": ms_batch / ms_solo,
+            "beams": len(beams), "adds_per_step": adds, "batch_equals_plain": same, "gpu_launches": args.steps,
             "config": {"workload": f"{len(beams)} uneven beams (channels 32/256/1024, DMs 256/1024/4096, "
-                                   f"10k-200k samples, Apertif/LOFAR grids, mixed uint8/float32), seed {args.seed}"}}
+                                   f"10k-200k samples, Apertif/LOFAR grids, mixed uint8/float32), seed {args.seed}; "
+                                   f"tuning budget {args.tune_budget} s per setup"}}
     print(json.dumps(line), flush=True)
     return 0 if same else 1
 
@@ -884,6 +906,7 @@ def main():
     ap.add_argument("--no-extra", action="store_true",
                     help="default run: skip the uint8, LOFAR, streamed and serving lines beside the headline")
     ap.add_argument("--serve-beams", type=int, default=40, help="beams of the default run's short serving line")
+    ap.add_argument("--tune-budget", type=float, default=1.5, help="batched: dd_tune budget per setup (s)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

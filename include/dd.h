@@ -329,6 +329,16 @@ dd_status dd_boxcar_snr_noalloc(const float* x, int64_t row_stride, int32_t n_ro
 dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, int32_t n);
 dd_status dd_batch_run(dd_batch_t batch, const void* const* ins, const int64_t* in_strides,
                        void* const* outs, const int64_t* out_strides, void* stream);
+/*
+ * Auto-tune a batch (Section 2.2 / 4.1: the best configuration depends on the
+ * setup): dd_tune (same budget and database rules) runs once per distinct
+ * setup of the batch (device, geometry and dtype), longest beams first, and
+ * every plan of that setup takes the chosen configuration, so the batch's
+ * beams run their tuned kernels.  This changes the plans' selected
+ * configurations.  *n_tuned (nullable) receives the number of setups tuned.
+ * The next dd_batch_run records its graph again.
+ */
+dd_status dd_batch_tune(dd_batch_t batch, double budget_s, const char* db_path, int32_t* n_tuned);
 dd_status dd_batch_destroy(dd_batch_t batch);
 
 /* -------------------------------------------------------------- streaming */

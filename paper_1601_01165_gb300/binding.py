@@ -83,6 +83,7 @@ def _declare(lib):
         "dd_batch_create": (st, [ctypes.POINTER(vp), ctypes.POINTER(vp), i32]),
         "dd_batch_run": (st, [vp, ctypes.POINTER(vp), P64, ctypes.POINTER(vp), P64, vp]),
         "dd_batch_destroy": (st, [vp]),
+        "dd_batch_tune": (st, [vp, dbl, ctypes.c_char_p, P32]),
         "dd_stream_create": (st, [ctypes.POINTER(vp), vp, i64]),
         "dd_stream_push": (st, [vp, vp, vp, P64, vp]),
         "dd_stream_reset": (st, [vp, vp]),
@@ -379,6 +380,13 @@ class Batch:
         os_arr = (ctypes.c_int64 * n)(*[o.stride(0) for o in outs])
         check(load().dd_batch_run(self._h, i_arr, is_arr, o_arr, os_arr, _stream_handle(stream)), "dd_batch_run")
         return outs
+
+    def tune(self, budget_s: float = 0.0, db_path: str | None = None) -> int:
+        """dd_batch_tune: tune each distinct setup once; returns the number of setups tuned."""
+        n = ctypes.c_int32()
+        check(load().dd_batch_tune(self._h, float(budget_s), db_path.encode() if db_path else None,
+                                   ctypes.byref(n)), "dd_batch_tune")
+        return n.value
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

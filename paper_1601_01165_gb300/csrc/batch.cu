@@ -16,6 +16,8 @@
 #include <cstring>
 #include <new>
 #include <numeric>
+#include <string>
+#include <utility>
 #include <vector>
 
 #include "dd_errors.h"
@@ -177,6 +179,45 @@ extern "C" dd_status dd_batch_run(dd_batch_t b, const void* const* ins, const in
   e = cudaGraphLaunch(b->exec, s);
   if (e != cudaSuccess) return set_cuda_error("dd_batch_run: graph launch", e);
   return DD_OK;
+}
+
+extern "C" dd_status dd_batch_tune(dd_batch_t b, double budget_s, const char* db_path, int32_t* n_tuned) {
+  NvtxRange range("dd_batch_tune");
+  clear_error();
+  if (!b) return set_error(DD_ERR_ARG, "dd_batch_tune: batch is NULL");
+  // one dd_tune per distinct setup (device, geometry, dtype), longest beams
+  // first; every other beam of a setup takes the same configuration
+  std::vector<std::pair<std::string, std::string>> done;  // key -> configuration name
+  int32_t tuned = 0;
+  int prev = 0;
+  cudaGetDevice(&prev);
+  cudaSetDevice(b->device);
+  dd_status st = DD_OK;
+  for (int k : b->order) {
+    dd_plan_s* p = b->plans[k];
+    const std::string key = tune_key_of(*p);
+    const std::string* name = nullptr;
+    for (const auto& kv : done)
+      if (kv.first == key) name = &kv.second;
+    if (name) {
+      for (size_t j = 0; j < p->configs.size(); ++j)
+        if (p->configs[j].name == *name) p->selected = (int)j;
+      continue;
+    }
+    st = dd_tune(p, budget_s, db_path, nullptr);
+    if (st != DD_OK) break;
+    done.emplace_back(key, p->configs[p->selected].name);
+    ++tuned;
+  }
+  cudaSetDevice(prev);
+  // the selections changed: record the graph again on the next run
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  b->key_in.clear();
+  if (n_tuned) *n_tuned = tuned;
+  return st;
 }
 
 extern "C" dd_status dd_batch_destroy(dd_batch_t b) {

@@ -64,6 +64,8 @@ struct FwdArgs {
 // Select the configuration recorded for this plan in the database named by
 // the DD_TUNE_DB environment variable, if there is one (tune.cpp).
 void apply_tune_db(dd_plan_s* plan);
+// The tuning database key of a plan: device name, geometry and dtype (tune.cpp).
+std::string tune_key_of(const dd_plan_s& p);
 
 // TMW6 needs 16-byte aligned input rows of a multiple of 32 floats (128 bytes).
 bool tmw6_accepts(const void* in, int64_t in_stride);
@@ -80,6 +82,9 @@ cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs&
 // table is filled in (dd_plan.cpp).
 dd_status finish_plan(dd_plan_s* p);
 void free_plan_device(dd_plan_s* p);
+// Indices of a plan's configurations, most promising first (the measured
+// preference list, then the rest of the menu, the generic kernels last).
+std::vector<int> config_preference_order(const dd_plan_s& p);
 // Validated forward launch (dd_api.cpp); cfg_override < 0 uses the plan's choice.
 dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
                          int64_t out_stride, cudaStream_t stream, int cfg_override);

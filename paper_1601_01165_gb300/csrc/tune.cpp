@@ -2,8 +2,8 @@
 // meaningful combinations and keeping the fastest; Section 4.1: the optimum
 // differs between platforms and observational setups).  dd_tune times every
 // valid configuration of a plan with CUDA events (median of repeats, after a
-// warm-up), keeps the fastest, and can record / reuse the choice in a
-// JSON-lines database keyed by device name and plan geometry.
+// warm-up), most promising first, keeps the fastest, and can record / reuse
+// the choice in a JSON-lines database keyed by device name and plan geometry.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,6 +30,8 @@ static std::string tune_key(const dd_plan_s& p) {
     std::snprintf(buf + std::strlen(buf), sizeof(buf) - std::strlen(buf), "|dm_index0=%d", p.dm_index0);
   return buf;
 }
+
+std::string tune_key_of(const dd_plan_s& p) { return tune_key(p); }
 
 // Look for `"key": "<key>"` in the database; on a hit return the stored config name and time.
 static bool db_lookup(const char* path, const std::string& key, std::string& cfg, double& ms) {
@@ -116,7 +118,10 @@ extern "C" dd_status dd_tune(dd_plan_t plan, double budget_s, const char* db_pat
   const auto wall0 = std::chrono::steady_clock::now();
   std::vector<double> med(plan->configs.size(), -1.0);
   int best = -1;
-  for (size_t k = 0; k < plan->configs.size(); ++k) {
+  // most promising configurations first, so that a time budget cut short
+  // still has the good ones timed
+  for (const int ki : config_preference_order(*plan)) {
+    const size_t k = (size_t)ki;
     if (budget_s > 0 && best >= 0) {
       const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - wall0).count();
       if (el > budget_s) break;

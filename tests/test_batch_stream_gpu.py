@@ -75,6 +75,34 @@ def test_batch_equals_solo_forward(dd):
     batch.close()
 
 
+def test_batch_tune_once_per_setup(dd, tmp_path):
+    """dd_batch_tune runs dd_tune once per distinct setup (here two beams
+    share each of three setups); beams of one setup take one configuration,
+    the tuned batch still equals solo launches and the oracle, and the
+    database then holds one record per setup."""
+    base = _small_batch(3)[:3]
+    beams = base + base            # every setup twice
+    plans, xs, hosts = _inputs(dd, beams, 20)
+    batch = dd.Batch(plans)
+    db = str(tmp_path / "batch.jsonl")
+    assert batch.tune(budget_s=0.0, db_path=db) == 3
+    for k in range(3):
+        assert plans[k].selected == plans[k + 3].selected
+    with open(db) as f:
+        assert len([json.loads(line) for line in f]) == 3
+    outs = [torch.empty((p.n_dm, p.n_out), dtype=p.out_dtype, device="cuda") for p in plans]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.run(xs, outs, stream=stream)
+    stream.synchronize()
+    for (s, dt), p, x, h, o in zip(beams, plans, xs, hosts, outs):
+        assert p.device_status() == 0
+        assert torch.equal(o, p.forward(x)), s.name
+        ref, scale = oracle_window(oracle_table(s), h, dt, 0, s.n_dm, 0, s.n_out)
+        assert_parity(o.cpu().numpy(), ref, scale, dt, where=f"tuned batch {s.name}")
+    batch.close()
+
+
 def test_batch_rejects_unaligned(dd):
     s = synth.Setup("una", 32, 1420.0, 2.0, 50e-6, 0.0, 0.25, 16, 1000)
     p = dd.Plan.from_setup(s, "f32")
