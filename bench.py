@@ -49,10 +49,10 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # keyed by (setup name, output samples, kernel config, dtype); valid only while
 # the kernel source hash matches.
 NCU_TRAFFIC = {
-    # 113.4 MB read + 128.7 MB written
-    ("apertif", 20000, "tmw6_f32_d6_t4096", "f32"): {"bytes": 242_039_296, "hash": "0c415d9b453f6fd2"},
-    # 33.0 MB read + 112.8 MB written
-    ("apertif", 20000, "u8pk_w8x1_d4_c24_st3", "u8"): {"bytes": 145_724_928, "hash": "0c415d9b453f6fd2"},
+    # fwd_tmw9_kernel<0>: 110.8 MB read + 122.6 MB written
+    ("apertif", 20000, "tmw9_f32_d9_t4096", "f32"): {"bytes": 233_434_624, "hash": "bda16fccfcf36ce6"},
+    # fwd_u8pk_kernel<8,1,4,24,3>: 33.0 MB read + 111.8 MB written
+    ("apertif", 20000, "u8pk_w8x1_d4_c24_st3", "u8"): {"bytes": 144_827_392, "hash": "bda16fccfcf36ce6"},
 }
 
 
@@ -72,7 +72,7 @@ def _kernel_hash():
     import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1601_01165_gb300", "csrc")
-    for name in ("fwd_kernels.cu", "fwd_tmw6.cu", "ptx.cuh", "dd_internal.h"):
+    for name in ("fwd_kernels.cu", "fwd_tmw6.cu", "fwd_tmw9.cu", "ptx.cuh", "dd_internal.h"):
         with open(os.path.join(csrc, name)) as f:
             text = f.read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
