@@ -636,10 +636,14 @@ def run_ours(args, setup):
 
 def run_batched(args):
     """64 uneven beams (Section 5.1: many beams per device): the batch (one
-    CUDA-graph launch of every beam's forward, beams dealt to internal streams
-    longest first) against 64 plain launches of the same plans, first with each
-    plan's default configuration, then after dd_batch_tune has tuned each
-    distinct setup once (both forms then run the tuned kernels)."""
+    CUDA-graph launch: persistent launches per configuration group, each
+    taking its beams' tiles longest first, and single launches for the other
+    beams, spread over internal streams) against 64 plain launches of the same
+    plans, first with each plan's default configuration, then after
+    dd_batch_tune has tuned each distinct setup once and timed each persistent
+    group against its beams' own launches (both forms then run the tuned
+    kernels); also the same graph with one launch per beam and with every
+    group persistent."""
     import torch
     from paper_1601_01165_gb300 import binding as dd
     torch.cuda.set_device(0)
@@ -693,7 +697,12 @@ def run_batched(args):
     t0 = time.perf_counter()
     n_setups = batch.tune(budget_s=args.tune_budget)
     tune_s = time.perf_counter() - t0
-    ms_batch = timed(run_batch, args.steps)
+    ms_batch = timed(run_batch, args.steps)     # persistent groups where tuning measured them faster
+    batch.set_persistent(0)                     # the same graph with one launch per beam
+    ms_batch_per_beam = timed(run_batch, args.steps)
+    batch.set_persistent(2)                     # every group that can be persistent
+    ms_batch_all_persistent = timed(run_batch, args.steps)
+    batch.set_persistent(1)
     ms_plain = timed(run_plain, args.steps)
     ms_solo = solo_sum()
     # the batch's results equal the per-beam launches (checked on every beam)
@@ -708,6 +717,9 @@ def run_batched(args):
             "default_configs": {"batch_ms": ms_batch_def, "plain_launches_ms": ms_plain_def,
                                 "speedup_vs_plain": ms_plain_def / ms_batch_def},
             "tuned_over_default_batch": ms_batch_def / ms_batch, "setups_tuned": n_setups, "tune_s": tune_s,
+            "graph_one_launch_per_beam_ms": ms_batch_per_beam,
+            "graph_every_group_persistent_ms": ms_batch_all_persistent,
+            "batch_over_one_launch_per_beam": ms_batch_per_beam / ms_batch,
             "sum_of_solo_launch_ms": ms_solo, "batch_over_solo_sum": ms_batch / ms_solo,
             "beams": len(beams), "adds_per_step": adds, "batch_equals_plain": same, "gpu_launches": args.steps,
             "config": {"workload": f"{len(beams)} uneven beams (channels 32/256/1024, DMs 256/1024/4096, "

@@ -309,22 +309,32 @@ dd_status dd_boxcar_snr_noalloc(const float* x, int64_t row_stride, int32_t n_ro
 /*
  * Many independent beams (Section 2: each beam is processed independently;
  * Section 5.1: many beams per device) launched as one CUDA graph.
- * dd_batch_create orders the n plans longest first and deals them to a few
- * internal streams by accumulated work (C * n_dm * n_out), so beams too small
- * to fill the GPU run side by side; the plans must outlive the batch and live
- * on the same device.  Mixed uint8 and float32 plans are allowed.
+ * dd_batch_create orders the n plans longest first (C * n_dm * n_out); the
+ * plans must outlive the batch and live on the same device.  Mixed uint8 and
+ * float32 plans are allowed.
  * dd_batch_run: ins[b] / outs[b] are device pointers for beam b with row
  * strides in_strides[b] / out_strides[b] (host arrays of n entries).  Each
- * beam runs the forward launch of its own plan's selected configuration with
- * NULL weights, so results are bit-identical to n separate dd_forward calls.
- * The first run on a stream records the fork from `stream`, the n launches
- * and the join into a CUDA graph keyed by the pointer set; later runs with the
- * same pointers replay it with one launch (a run on the legacy NULL stream
- * launches directly).  Work queued on `stream` after the run waits for every
- * beam.  Inputs must be 16-byte aligned with 16-byte row pitches
- * (DD_ERR_ALIGN otherwise).  Runs of one batch must not overlap in time (they
- * share the batch's internal streams).  An expired bounded wait in a beam's
- * kernel is reported in that beam's plan status word (dd_plan_device_status).
+ * beam runs the configuration dd_forward would run for it (its plan's
+ * selection, resolved for its input layout) with NULL weights, so results are
+ * bit-identical to n separate dd_forward calls.  Beams whose configurations
+ * have a persistent form (the staged, packed-uint8 and 9-trial Tensor-Memory
+ * kernels) may share one persistent launch per configuration (and blocks per
+ * SM; at most 64 beams each): its blocks take the group's tiles, longest beam
+ * first, from a work counter until none are left.  Which groups run that way
+ * is set by dd_batch_set_persistent; the other beams get one launch each.
+ * The launches are dealt to a few internal streams by accumulated work.  The
+ * first run on a stream with a given pointer set synchronizes `stream` once,
+ * uploads the persistent groups' tensor maps and counters (library-owned
+ * device memory) and records the fork from `stream`, the counter resets, the
+ * launches and the join into a CUDA graph; later runs with the same pointers
+ * replay it with one launch (a run on the legacy NULL stream launches
+ * directly).  Work queued on `stream` after the run waits for every beam.
+ * Inputs must be 16-byte aligned with 16-byte row pitches (DD_ERR_ALIGN
+ * otherwise).  Runs of one batch must not overlap in time (they share the
+ * batch's internal streams and device work).  An expired bounded wait in a
+ * beam's kernel is reported in that beam's plan status word
+ * (dd_plan_device_status; a persistent launch reports it to the beam whose
+ * tile timed out and stops).
  */
 dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, int32_t n);
 dd_status dd_batch_run(dd_batch_t batch, const void* const* ins, const int64_t* in_strides,
@@ -335,10 +345,22 @@ dd_status dd_batch_run(dd_batch_t batch, const void* const* ins, const int64_t* 
  * setup of the batch (device, geometry and dtype), longest beams first, and
  * every plan of that setup takes the chosen configuration, so the batch's
  * beams run their tuned kernels.  This changes the plans' selected
- * configurations.  *n_tuned (nullable) receives the number of setups tuned.
- * The next dd_batch_run records its graph again.
+ * configurations.  It then times every group of beams that could share a
+ * persistent launch against the same beams' own launches (one after another,
+ * best of three, on scratch buffers of the largest beam's size, allocated and
+ * freed here) and records which form was faster for dd_batch_set_persistent
+ * mode 1.  *n_tuned (nullable) receives the number of setups tuned.  The next
+ * dd_batch_run records its graph again.
  */
 dd_status dd_batch_tune(dd_batch_t batch, double budget_s, const char* db_path, int32_t* n_tuned);
+/* Which configuration groups dd_batch_run gives one persistent launch:
+ * mode 0: none (one launch per beam); mode 1 (the default): those that
+ * dd_batch_tune measured faster than their beams' own launches, and, untimed,
+ * groups of the 9-trial Tensor-Memory kernel and of packed-uint8 shapes with
+ * at most two trials per warp (the kinds that measured so on GB300); mode 2:
+ * every group that can have one.  DD_ERR_ARG for another mode.  The next
+ * dd_batch_run records its graph again. */
+dd_status dd_batch_set_persistent(dd_batch_t batch, int32_t mode);
 dd_status dd_batch_destroy(dd_batch_t batch);
 
 /* -------------------------------------------------------------- streaming */

@@ -84,6 +84,7 @@ def _declare(lib):
         "dd_batch_run": (st, [vp, ctypes.POINTER(vp), P64, ctypes.POINTER(vp), P64, vp]),
         "dd_batch_destroy": (st, [vp]),
         "dd_batch_tune": (st, [vp, dbl, ctypes.c_char_p, P32]),
+        "dd_batch_set_persistent": (st, [vp, i32]),
         "dd_stream_create": (st, [ctypes.POINTER(vp), vp, i64]),
         "dd_stream_push": (st, [vp, vp, vp, P64, vp]),
         "dd_stream_reset": (st, [vp, vp]),
@@ -387,6 +388,13 @@ class Batch:
         check(load().dd_batch_tune(self._h, float(budget_s), db_path.encode() if db_path else None,
                                    ctypes.byref(n)), "dd_batch_tune")
         return n.value
+
+    def set_persistent(self, mode: int = 1):
+        """dd_batch_set_persistent: 0 (or False) one launch per beam; 1 (or True, the
+        default) persistent launches where tuning measured them faster, else by kernel
+        kind; 2 a persistent launch for every group that can have one."""
+        mode = int(mode)
+        check(load().dd_batch_set_persistent(self._h, mode), "dd_batch_set_persistent")
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

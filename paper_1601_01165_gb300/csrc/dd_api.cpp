@@ -32,20 +32,15 @@ dd_status set_cuda_error(const char* where, cudaError_t e) {
 
 void clear_error() { g_last_error.clear(); }
 
-// Launch of the selected (or a fallback) forward kernel over output samples
-// [t0, t1) (arguments already validated; t0 a multiple of 128 samples keeps
-// every alignment the kernels rely on).
-static dd_status launch_range(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
-                              int64_t out_stride, int64_t t0, int64_t t1, cudaStream_t stream, int cfg_override) {
+FwdArgs plan_args(const dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
+                  int64_t out_stride, int64_t t0, int64_t t1) {
   const int elem = p->dtype == DD_U8_I32 ? 1 : 4;
-  in = static_cast<const unsigned char*>(in) + t0 * elem;
-  out = static_cast<unsigned char*>(out) + t0 * 4;
   FwdArgs a{};
-  a.in = in;
+  a.in = static_cast<const unsigned char*>(in) + t0 * elem;
   a.in_stride = in_stride;
   a.in_avail = in_stride - t0;
   a.w = w;
-  a.out = out;
+  a.out = static_cast<unsigned char*>(out) + t0 * 4;
   a.out_stride = out_stride;
   a.delays = p->d_delays;
   a.delaysT = p->d_delaysT;
@@ -57,11 +52,16 @@ static dd_status launch_range(dd_plan_s* p, const void* in, int64_t in_stride, c
   a.n_out = t1 - t0;
   a.n_in = (t1 - t0) + p->max_delay;
   a.status = p->d_status;
-  int k = cfg_override >= 0 ? cfg_override : p->selected;
+  return a;
+}
+
+const TileConfig* resolve_config(const dd_plan_s* p, const FwdArgs& a, int cfg_override) {
+  const int elem = p->dtype == DD_U8_I32 ? 1 : 4;
+  const int k = cfg_override >= 0 ? cfg_override : p->selected;
   const TileConfig* cfg = &p->configs[k];
   // Bulk copies need a 16-byte aligned source and row pitch; otherwise use the
   // plain-load kernel, which computes the same sums.
-  const bool aligned = ((uintptr_t)in % 16 == 0) && ((in_stride * elem) % 16 == 0);
+  const bool aligned = ((uintptr_t)a.in % 16 == 0) && ((a.in_stride * elem) % 16 == 0);
   auto first_of = [&](Kind kind) -> const TileConfig* {
     for (size_t j = 0; j < p->configs.size(); ++j)
       if (p->configs[j].kind == kind) return &p->configs[j];
@@ -70,11 +70,21 @@ static dd_status launch_range(dd_plan_s* p, const void* in, int64_t in_stride, c
   if (cfg->kind != Kind::Naive && !aligned) cfg = first_of(Kind::Naive);
   // TMW9 needs spare samples after each row, else TMW6 (if offered) takes it;
   // TMW6 stages 128-byte rows; other layouts take the preferred shared-memory kernel
-  if (cfg->kind == Kind::TmW9 && !tmw9_accepts(in, in_stride, a.n_in)) {
+  if (cfg->kind == Kind::TmW9 && !tmw9_accepts(a.in, a.in_stride, a.n_in)) {
     const TileConfig* t6 = first_of(Kind::TmW6);
     cfg = t6 ? t6 : &p->configs[p->fallback];
   }
-  if (cfg->kind == Kind::TmW6 && !tmw6_accepts(in, in_stride)) cfg = &p->configs[p->fallback];
+  if (cfg->kind == Kind::TmW6 && !tmw6_accepts(a.in, a.in_stride)) cfg = &p->configs[p->fallback];
+  return cfg;
+}
+
+// Launch of the selected (or a fallback) forward kernel over output samples
+// [t0, t1) (arguments already validated; t0 a multiple of 4096 samples keeps
+// every alignment the kernels rely on).
+static dd_status launch_range(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
+                              int64_t out_stride, int64_t t0, int64_t t1, cudaStream_t stream, int cfg_override) {
+  const FwdArgs a = plan_args(p, in, in_stride, w, out, out_stride, t0, t1);
+  const TileConfig* cfg = resolve_config(p, a, cfg_override);
   cudaError_t e = launch_forward(*cfg, p->dtype, a, stream);
   if (e != cudaSuccess) return set_cuda_error("dd_forward: launch", e);
   return DD_OK;

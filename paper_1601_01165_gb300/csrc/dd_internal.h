@@ -61,6 +61,70 @@ struct FwdArgs {
   int* status;             // device error word
 };
 
+// ------------------------------------------------------------- batches
+// One beam of a persistent batch launch: its forward arguments, its staged
+// row pitch (staged / U8PK configurations), the x extent of the grid its
+// plain launch would have, and its first work item.
+struct BatchBeam {
+  FwdArgs a;
+  int pitch;
+  int nx;
+  int first;
+  int pad_;
+};
+// A persistent launch's work, passed whole as the kernel's parameter (read-only
+// constant-bank data, which the compiler may reload at will, where arguments in
+// global memory would be reloaded after every barrier wait): beams[0 ..
+// n_beams) in the order their items are numbered (longest first), n_items
+// tiles in all, and the counter the blocks take items from (zeroed before the
+// launch).  Item j of a beam is the plain launch's block (x = j % nx, y = j /
+// nx).  TMW9 beams' eight tensor maps each sit in global memory (`maps`,
+// [n_beams][8], 64-byte aligned).
+constexpr int kBeamsPerLaunch = 64;  // 64 x 128 bytes of beams: 8 KB of parameters
+struct BatchWork {
+  const void* maps;
+  int n_beams;
+  int n_items;
+  int* counter;
+  BatchBeam beams[kBeamsPerLaunch];
+};
+struct WorkItem {
+  int beam, x, y;
+};
+
+#ifdef __CUDACC__
+// Every thread of the block: take the next item (false when the list is
+// exhausted).  item_s is a shared word of the block.
+__device__ __forceinline__ bool next_item(const BatchWork& w, int& item_s, WorkItem& it) {
+  if (threadIdx.x == 0) item_s = atomicAdd(w.counter, 1);
+  __syncthreads();
+  const int item = item_s;
+  __syncthreads();  // every thread has read item_s before the next item overwrites it
+  if (item >= w.n_items) return false;
+  int lo = 0, hi = w.n_beams - 1;  // the last beam whose first item <= item
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (w.beams[mid].first <= item) lo = mid;
+    else hi = mid - 1;
+  }
+  const int j = item - w.beams[lo].first, nx = w.beams[lo].nx;
+  it.beam = lo;
+  it.x = j % nx;
+  it.y = j / nx;
+  return true;
+}
+
+// Every thread of the block: copy beam `k` of the work to `beam_s` (shared
+// memory) for a tile that reads its arguments there.  The caller has made
+// sure that no thread still reads the previous beam.
+__device__ __forceinline__ void copy_beam(const BatchWork& w, int k, BatchBeam& beam_s) {
+  static_assert(sizeof(BatchBeam) % 4 == 0 && sizeof(BatchBeam) / 4 <= 64, "one word per thread");
+  if (threadIdx.x < sizeof(BatchBeam) / 4)
+    reinterpret_cast<int*>(&beam_s)[threadIdx.x] = reinterpret_cast<const int*>(&w.beams[k])[threadIdx.x];
+  __syncthreads();
+}
+#endif
+
 // Select the configuration recorded for this plan in the database named by
 // the DD_TUNE_DB environment variable, if there is one (tune.cpp).
 void apply_tune_db(dd_plan_s* plan);
@@ -85,6 +149,30 @@ void free_plan_device(dd_plan_s* p);
 // Indices of a plan's configurations, most promising first (the measured
 // preference list, then the rest of the menu, the generic kernels last).
 std::vector<int> config_preference_order(const dd_plan_s& p);
+// Forward arguments of a plan over output samples [t0, t1) (dd_api.cpp), and
+// the configuration a launch with them runs: the plan's choice (or
+// cfg_override >= 0), unless the input's layout needs another one.
+FwdArgs plan_args(const dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
+                  int64_t out_stride, int64_t t0, int64_t t1);
+const TileConfig* resolve_config(const dd_plan_s* p, const FwdArgs& a, int cfg_override);
+// Persistent forms for batches (fwd_kernels.cu, fwd_tmw9.cu): does the
+// configuration have one, its dynamic shared memory for a staged row pitch,
+// its resident blocks per SM at that shared memory and the plain kernel's (0:
+// cannot launch), and the launch over a work list with `grid` blocks (at most
+// the resident ones, which then take every item in turn).  TMW9 beams need their eight tensor maps in the work's `maps`
+// (tmw9_encode_views writes them, tmw9_views_bytes of them per beam).
+bool has_persistent(const TileConfig& cfg, dd_dtype dtype);
+// Whether a group of this configuration runs persistent when no timing says otherwise.
+bool persistent_by_default(const TileConfig& cfg);
+int persistent_smem(const TileConfig& cfg, dd_dtype dtype, int pitch);
+int persistent_blocks_per_sm(const TileConfig& cfg, dd_dtype dtype, int smem);
+int plain_blocks_per_sm(const TileConfig& cfg, dd_dtype dtype, int smem);
+cudaError_t launch_persistent(const TileConfig& cfg, dd_dtype dtype, const BatchWork& w, int smem, int grid,
+                              cudaStream_t s);
+size_t tmw9_views_bytes();
+bool tmw9_encode_views(const FwdArgs& a, void* out);
+const void* tmw9_persistent_kernel();
+const void* tmw9_plain_kernel();
 // Validated forward launch (dd_api.cpp); cfg_override < 0 uses the plan's choice.
 dd_status forward_device(dd_plan_s* p, const void* in, int64_t in_stride, const float* w, void* out,
                          int64_t out_stride, cudaStream_t stream, int cfg_override);

@@ -16,6 +16,7 @@
 //          reads and global writes are contiguous across the warp.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "dd_internal.h"
@@ -95,6 +96,23 @@ __device__ __forceinline__ StageBars<STAGES>& init_stage_bars(unsigned char* sme
   return B;
 }
 
+// Fresh barriers for a persistent block's next tile.  Called by every thread
+// once the block is past its tile: every copy has landed (the copiers drained
+// them) and no thread waits on or arrives at the old barriers any more.
+template <int STAGES>
+__device__ __forceinline__ void reset_stage_bars(StageBars<STAGES>& B, int warps, int copiers) {
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_inval(&B.full[s]);
+      mbar_inval(&B.empty[s]);
+      mbar_init(&B.full[s], (uint32_t)copiers);
+      mbar_init(&B.empty[s], (uint32_t)warps);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+}
+
 // The warps of a STAGED or U8PK block copy their own input: chunk k
 // (channels [k CC, k CC + CC)) goes to stage k % STAGES, one lane per slot j
 // (the span of channel k CC + j and its BD delays).  With SPREAD every warp
@@ -143,7 +161,8 @@ __device__ __forceinline__ void stage_issue(const FwdArgs& a, int pitch, int64_t
 }
 
 // A copying warp's side of the pipeline: `kn` is the next chunk it stages
-// and (dlo, dhi) its lanes' delays for it.
+// and (dlo, dhi) its lanes' delays for it.  Every tile starts on fresh
+// barriers (a persistent block resets them between tiles).
 template <typename Tin, int BD, int CC, int STAGES, int NW, bool SPREAD>
 struct Stager {
   static_assert(STAGES >= 2, "chunk k + 1 is staged while chunk k is read");
@@ -225,9 +244,11 @@ __device__ __forceinline__ void stage_release(StageBars<STAGES>& B, int k, int l
   if (lane == 0) mbar_arrive(&B.empty[k % STAGES]);
 }
 
-// One tile: DM trials [by*BD, by*BD + BD) x samples [bx*BT, bx*BT + BT).
+// One tile: DM trials [i0, i0 + BD) x samples [t0, t0 + BT), on fresh stage
+// barriers.  False after a timeout (also reported in the status word).
 template <typename Tin, bool WEIGHTED, int BD, int BT, int CC, int STAGES>
-__global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
+__device__ __forceinline__ bool staged_tile(const FwdArgs& a, int pitch, int64_t t0, int i0,
+                                            StageBars<STAGES>& B, unsigned char* smem_raw) {
   using Tacc = typename AccOf<Tin>::type;
   constexpr int V = 16 / (int)sizeof(Tin);  // elements per 16 bytes
   constexpr int NW = 8;
@@ -236,20 +257,16 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
   static_assert(BD % NW == 0 && BT % 64 == 0 && BD % 4 == 0, "tile shape (an even number of samples per lane)");
   // a block's delay slice [i0, i0 + BD) must stay inside the padded row
   static_assert(kDmPad % BD == 0, "BD must divide the trial padding");
-
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   using Pipe = Stager<Tin, BD, CC, STAGES, NW, false>;
-  StageBars<STAGES>& B = init_stage_bars<STAGES>(smem_raw, NW, Pipe::kCopiers);
   Tin* sin = reinterpret_cast<Tin*>(smem_raw + kStBarBytes);
   int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes + (size_t)STAGES * CC * pitch * sizeof(Tin));
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t t0 = (int64_t)blockIdx.x * BT;
-  const int i0 = blockIdx.y * BD;
   const int nt = (int)min((int64_t)BT, a.n_out - t0);
   const int nchunks = (a.C + CC - 1) / CC;
 
   Pipe st{a, pitch, t0, nt, i0, nchunks, warp, lane, B, sin, sdel};
+  bool ok = true;
   if (st.copies()) st.prologue();
 
   Tacc acc[DPW][SPL];
@@ -258,8 +275,7 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
 #pragma unroll
     for (int q = 0; q < SPL; ++q) acc[m][q] = 0;
 
-  bool ok = true;
-  for (int k = 0; k < nchunks; ++k) {
+  for (int k = 0; k < nchunks && ok; ++k) {
     if (st.copies() && !st.ahead(k)) {
       ok = false;
       break;
@@ -304,7 +320,7 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
   if (st.copies()) st.drain();
   if (!ok) {
     if (lane == 0) report_error(a.status, kDevWaitTimeout);
-    return;
+    return false;
   }
 
   Tacc* __restrict__ out = static_cast<Tacc*>(a.out);
@@ -318,6 +334,36 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
         if (tt < nt) out[(int64_t)i * a.out_stride + t0 + tt] = acc[m][q];
       }
     }
+  }
+  return true;
+}
+
+template <typename Tin, bool WEIGHTED, int BD, int BT, int CC, int STAGES>
+__global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  StageBars<STAGES>& B = init_stage_bars<STAGES>(smem_raw, 8, Stager<Tin, BD, CC, STAGES, 8, false>::kCopiers);
+  (void)staged_tile<Tin, WEIGHTED, BD, BT, CC, STAGES>(a, pitch, (int64_t)blockIdx.x * BT, blockIdx.y * BD, B,
+                                                        smem_raw);
+}
+
+// Persistent form for batches: the block takes tiles of many beams from the
+// work list until it is exhausted (see BatchWork), each tile exactly as a
+// block of the plain kernel runs it, on stage barriers reset in between.
+template <typename Tin, bool WEIGHTED, int BD, int BT, int CC, int STAGES>
+__global__ void __launch_bounds__(256) fwd_staged_persistent(const __grid_constant__ BatchWork w) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  constexpr int kCopiers = Stager<Tin, BD, CC, STAGES, 8, false>::kCopiers;
+  StageBars<STAGES>& B = init_stage_bars<STAGES>(smem_raw, 8, kCopiers);
+  __shared__ int item_s;
+  __shared__ BatchBeam beam_s;  // the tile's arguments, at fixed shared addresses
+  while (true) {
+    WorkItem it;
+    if (!next_item(w, item_s, it)) break;
+    copy_beam(w, it.beam, beam_s);
+    const bool ok = staged_tile<Tin, WEIGHTED, BD, BT, CC, STAGES>(beam_s.a, beam_s.pitch, (int64_t)it.x * BT,
+                                                                    it.y * BD, B, smem_raw);
+    if (__syncthreads_or(!ok)) break;
+    reset_stage_bars<STAGES>(B, 8, kCopiers);
   }
 }
 
@@ -336,31 +382,38 @@ __global__ void __launch_bounds__(256) fwd_staged_kernel(FwdArgs a, int pitch) {
 // cleared, so the result is the exact integer sum.  The sums are formed with
 // integer multiply-adds by a run-time 1 so that they issue to the FMA pipe,
 // leaving the ALU pipe to the byte permutes (two per word and channel).
+template <int WD, int WT, int DPW>
+struct U8PkShape {
+  static constexpr int KW = 7;        // words per lane
+  static constexpr int SPL = 4 * KW;  // samples per lane
+  static constexpr int BD = WD * DPW;
+  static constexpr int BT = 32 * SPL * WT;
+};
+
+// One tile: DM trials [i0, i0 + BD) x samples [t0, t0 + BT), on fresh stage
+// barriers.  False after a timeout (also reported).
 template <int WD, int WT, int DPW, int CC, int STAGES>
-__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int pitch) {
+__device__ __forceinline__ bool u8pk_tile(const FwdArgs& a, int pitch, int64_t t0, int i0,
+                                          StageBars<STAGES>& B, unsigned char* smem_raw) {
   constexpr int V = 16;
   constexpr int NW = WD * WT;
-  constexpr int KW = 7;               // words per lane
-  constexpr int SPL = 4 * KW;         // samples per lane
-  constexpr int BD = WD * DPW;
-  constexpr int BT = 32 * SPL * WT;
+  constexpr int KW = U8PkShape<WD, WT, DPW>::KW;
+  constexpr int SPL = U8PkShape<WD, WT, DPW>::SPL;
+  constexpr int BD = U8PkShape<WD, WT, DPW>::BD;
+  constexpr int BT = U8PkShape<WD, WT, DPW>::BT;
   static_assert(BD % 4 == 0 && BT % 16 == 0, "tile shape");
   static_assert(kDmPad % BD == 0, "BD must divide the trial padding");
-
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   using Pipe = Stager<uint8_t, BD, CC, STAGES, NW, true>;
-  StageBars<STAGES>& B = init_stage_bars<STAGES>(smem_raw, NW, Pipe::kCopiers);
   uint8_t* sin = smem_raw + kStBarBytes;
   int32_t* sdel = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes + (size_t)STAGES * CC * pitch);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int wd = warp % WD, wt = warp / WD;
-  const int64_t t0 = (int64_t)blockIdx.x * BT;
-  const int i0 = blockIdx.y * BD;
   const int nt = (int)min((int64_t)BT, a.n_out - t0);
   const int nchunks = (a.C + CC - 1) / CC;
 
   Pipe st{a, pitch, t0, nt, i0, nchunks, warp, lane, B, sin, sdel};
+  bool ok = true;
   if (st.copies()) st.prologue();
 
   uint32_t ra[DPW][KW], rb[DPW][KW];  // A and B of each word (see above)
@@ -471,8 +524,7 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
   };
 
   int since_flush = 0;
-  bool ok = true;
-  for (int k = 0; k < nchunks; ++k) {
+  for (int k = 0; k < nchunks && ok; ++k) {
     if (st.copies() && !st.ahead(k)) {
       ok = false;
       break;
@@ -535,9 +587,9 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
   if (!ok && lane == 0) report_error(a.status, kDevWaitTimeout);
   if constexpr (!kOutTotals) {
     // transpose through shared memory (every warp is past the channel loop
-    // and no copy is in flight, so the stage area is free)
-    __syncthreads();
-    if (!ok) return;
+    // and no copy is in flight, so the stage area is free); the block agrees
+    // on the outcome first, so every warp meets the barriers below or none
+    if (!__syncthreads_and(ok)) return false;
     int32_t* epi = reinterpret_cast<int32_t*>(smem_raw + kStBarBytes) + (size_t)warp * DPW * 32 * SPL;
 #pragma unroll
     for (int m = 0; m < DPW; ++m)
@@ -552,6 +604,37 @@ __global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int p
       int32_t* orow = out + (int64_t)i * a.out_stride + t0 + tw0;
       for (int u = lane; u < lim; u += 32) orow[u] = epi[m * 32 * SPL + u];
     }
+    // the next tile of a persistent block stages into this area again
+    __syncthreads();
+  }
+  return ok;
+}
+
+template <int WD, int WT, int DPW, int CC, int STAGES>
+__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_kernel(FwdArgs a, int pitch) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  using Sh = U8PkShape<WD, WT, DPW>;
+  StageBars<STAGES>& B =
+      init_stage_bars<STAGES>(smem_raw, WD * WT, Stager<uint8_t, Sh::BD, CC, STAGES, WD * WT, true>::kCopiers);
+  (void)u8pk_tile<WD, WT, DPW, CC, STAGES>(a, pitch, (int64_t)blockIdx.x * Sh::BT, blockIdx.y * Sh::BD, B, smem_raw);
+}
+
+// Persistent form for batches (see fwd_staged_persistent).
+template <int WD, int WT, int DPW, int CC, int STAGES>
+__global__ void __launch_bounds__(32 * WD * WT) fwd_u8pk_persistent(const __grid_constant__ BatchWork w) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  using Sh = U8PkShape<WD, WT, DPW>;
+  constexpr int kCopiers = Stager<uint8_t, Sh::BD, CC, STAGES, WD * WT, true>::kCopiers;
+  StageBars<STAGES>& B = init_stage_bars<STAGES>(smem_raw, WD * WT, kCopiers);
+  __shared__ int item_s;
+  while (true) {
+    WorkItem it;
+    if (!next_item(w, item_s, it)) break;
+    const BatchBeam& bm = w.beams[it.beam];  // kernel parameters
+    const bool ok =
+        u8pk_tile<WD, WT, DPW, CC, STAGES>(bm.a, bm.pitch, (int64_t)it.x * Sh::BT, it.y * Sh::BD, B, smem_raw);
+    if (__syncthreads_or(!ok)) break;
+    reset_stage_bars<STAGES>(B, WD * WT, kCopiers);
   }
 }
 
@@ -661,6 +744,108 @@ cudaError_t launch_forward(const TileConfig& cfg, dd_dtype dtype, const FwdArgs&
       return launch_u8pk(cfg, a, s);
   }
   return cudaErrorInvalidConfiguration;
+}
+
+// ------------------------------------------------------ persistent launches
+
+int u8pk_smem_for(const TileConfig& cfg, int pitch);
+int staged_smem_for(dd_dtype dtype, int stages, int cc, int bd, int pitch);
+
+// The persistent kernel of a configuration (PERSISTENT) or its plain
+// unweighted kernel, with its block size; null if there is none.
+template <bool PERSISTENT>
+static const void* kernel_of(const TileConfig& cfg, dd_dtype dtype, int* threads) {
+  switch (cfg.kind) {
+    case Kind::Staged:
+      *threads = 256;
+#define X(BD_, BT_, CC_, ST_)                                                                                   \
+  if (cfg.bd == BD_ && cfg.bt == BT_ && cfg.cc == CC_ && cfg.stages == ST_) {                              \
+    if (dtype == DD_U8_I32)                                                                                \
+      return PERSISTENT ? (const void*)fwd_staged_persistent<uint8_t, false, BD_, BT_, CC_, ST_>           \
+                        : (const void*)fwd_staged_kernel<uint8_t, false, BD_, BT_, CC_, ST_>;              \
+    return PERSISTENT ? (const void*)fwd_staged_persistent<float, false, BD_, BT_, CC_, ST_>               \
+                      : (const void*)fwd_staged_kernel<float, false, BD_, BT_, CC_, ST_>;                  \
+  }
+      DD_STAGED_CASES(X)
+#undef X
+      return nullptr;
+    case Kind::U8Pk: {
+      const int nw = cfg.threads / 32, wt = cfg.bt / (32 * 28), wd = nw / wt, dpw = cfg.bd / wd;
+      *threads = cfg.threads;
+#define X(WD_, WT_, DPW_, CC_, ST_)                                                                   \
+  if (wd == WD_ && wt == WT_ && dpw == DPW_ && cfg.cc == CC_ && cfg.stages == ST_)                \
+    return PERSISTENT ? (const void*)fwd_u8pk_persistent<WD_, WT_, DPW_, CC_, ST_>                 \
+                      : (const void*)fwd_u8pk_kernel<WD_, WT_, DPW_, CC_, ST_>;
+      DD_U8PK_CASES(X)
+#undef X
+      return nullptr;
+    }
+    case Kind::TmW9:
+      *threads = cfg.threads;
+      return PERSISTENT ? tmw9_persistent_kernel() : tmw9_plain_kernel();
+    default:
+      return nullptr;
+  }
+}
+
+// Measured on GB300 against the same beams' own launches: the TMW9 and the
+// one- or two-trial-per-warp U8PK persistent launches ran as fast or faster;
+// STAGED (its arguments reloaded from shared memory in a kernel bound by
+// shared-memory bandwidth) and four-trial U8PK ran 2-5 % slower.
+bool persistent_by_default(const TileConfig& cfg) {
+  if (cfg.kind == Kind::TmW9) return true;
+  if (cfg.kind != Kind::U8Pk) return false;
+  const int nw = cfg.threads / 32, wt = cfg.bt / (32 * 28), wd = nw / wt;
+  return cfg.bd / wd <= 2;
+}
+
+bool has_persistent(const TileConfig& cfg, dd_dtype dtype) {
+  int threads = 0;
+  return (cfg.kind == Kind::Staged || cfg.kind == Kind::U8Pk || cfg.kind == Kind::TmW9) &&
+         kernel_of<true>(cfg, dtype, &threads) != nullptr;
+}
+
+int persistent_smem(const TileConfig& cfg, dd_dtype dtype, int pitch) {
+  switch (cfg.kind) {
+    case Kind::Staged: return staged_smem_for(dtype, cfg.stages, cfg.cc, cfg.bd, pitch);
+    case Kind::U8Pk: return u8pk_smem_for(cfg, pitch);
+    case Kind::TmW9: return cfg.smem;
+    default: return 0;
+  }
+}
+
+// Resident blocks per SM of a kernel at `smem` bytes of dynamic shared memory (0: cannot launch).
+static int blocks_per_sm(const void* kern, int threads, int smem) {
+  int per_sm = 0;
+  if (!kern || cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess)
+    return 0;
+  return per_sm;
+}
+
+int persistent_blocks_per_sm(const TileConfig& cfg, dd_dtype dtype, int smem) {
+  int threads = 0;
+  const void* kern = kernel_of<true>(cfg, dtype, &threads);
+  return blocks_per_sm(kern, threads, smem);
+}
+
+int plain_blocks_per_sm(const TileConfig& cfg, dd_dtype dtype, int smem) {
+  int threads = 0;
+  const void* kern = kernel_of<false>(cfg, dtype, &threads);
+  return blocks_per_sm(kern, threads, smem);
+}
+
+cudaError_t launch_persistent(const TileConfig& cfg, dd_dtype dtype, const BatchWork& w, int smem, int grid,
+                              cudaStream_t s) {
+  if (w.n_items <= 0) return cudaSuccess;
+  int threads = 0;
+  const void* kern = kernel_of<true>(cfg, dtype, &threads);
+  if (!kern || grid < 1) return cudaErrorInvalidConfiguration;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  BatchWork arg = w;
+  void* args[] = {&arg};
+  return cudaLaunchKernel(kern, dim3(grid), dim3(threads), args, (size_t)smem, s);
 }
 
 std::vector<TileConfig> staged_menu(dd_dtype dtype) {

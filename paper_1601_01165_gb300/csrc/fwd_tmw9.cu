@@ -126,27 +126,10 @@ constexpr int kNPH = 6;
 __device__ constexpr int ph_trial(int f) { return f % 3; }
 __device__ constexpr int ph_col(int f) { return 16 * (f / 3); }
 
-template <bool WEIGHTED>
-__global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_constant__ Tmw9Maps maps, FwdArgs a) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  Hdr& H = *reinterpret_cast<Hdr*>(smem_raw);
-  const uint32_t sbase = smem_u32(smem_raw);
-  unsigned char* stages = smem_raw + (((sbase + kHdr + 1023u) & ~1023u) - sbase);
-
-  const int tid = threadIdx.x, lane = tid & 31;
-  // warp-uniform values go through a lane-0 broadcast, which lets the
-  // compiler keep them (and the TMEM addresses built from them) in uniform
-  // registers instead of moving each address over before each TMEM access
-  const int warp = __shfl_sync(0xffffffffu, tid >> 5, 0);
-  const int q = warp & 3, p = warp >> 2;
-  const int r = 32 * q + lane;  // TMEM lane of this thread
-  const int64_t t0 = (int64_t)blockIdx.y * kBT;
-  const int g = blockIdx.x;
-  const int i0 = g * kT;
-  const int C = a.C;
-  const int4* gdesc = a.nine_desc + (int64_t)g * C;  // this block's descriptors, one per channel
-
-  if (tid == 0) {
+// Block set-up shared by the plain and the persistent kernel: the stage
+// barriers, the status flag and the Tensor Memory allocation.
+__device__ __forceinline__ void tmw9_setup(Hdr& H, int warp) {
+  if (threadIdx.x == 0) {
     for (int w = 0; w < 12; ++w)
       for (int j = 0; j < kWS; ++j) mbar_init(&H.sfull[w][j], 1);
     H.failed = 0;
@@ -156,6 +139,33 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
+}
+
+__device__ __forceinline__ void tmw9_teardown(Hdr& H, int warp) {
+  tmem_fence_before_sync();
+  __syncthreads();
+  tmem_fence_after_sync();
+  if (warp == 0) tmem_dealloc(H.tbase, kCols);
+}
+
+// Own channels of warp p (channels c = p mod 3) among C.
+__device__ __forceinline__ int own_channels(int C, int p) { return C > p ? (C - 1 - p) / kLead + 1 : 0; }
+
+// One tile: trials [9 g, 9 g + 9) x samples [4096 ty, + 4096).  `mb` counts
+// this warp's own channels of the block's earlier tiles (a persistent block
+// runs tile after tile): the warp's m-th own channel of this tile is its
+// (mb + m)-th, which fixes its stage and that stage's barrier phase.  False
+// after a timeout (reported in the status word; no output written).
+template <bool WEIGHTED>
+__device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a, int g, int ty, int mb, Hdr& H,
+                                          unsigned char* stages, int warp) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int q = warp & 3, p = warp >> 2;
+  const int r = 32 * q + lane;  // TMEM lane of this thread
+  const int64_t t0 = (int64_t)ty * kBT;
+  const int i0 = g * kT;
+  const int C = a.C;
+  const int4* gdesc = a.nine_desc + (int64_t)g * C;  // this block's descriptors, one per channel
   const uint32_t tq = __shfl_sync(0xffffffffu, H.tbase, 0) + ((uint32_t)(32 * q) << 16);  // quadrant's lanes, column 0
 
   // ------------------------------------------------ this warp's tile loads
@@ -167,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   int issued = 0;  // own channels whose load was issued (lane 0)
   auto base_of = [&](int c) { return c < C ? __ldg(&gdesc[c].x) : 0; };
   auto issue = [&](int c, int base) {
-    const int m = (c - p) / kLead, j = m % kWS;
+    const int m = mb + (c - p) / kLead, j = m % kWS;
     unsigned char* st = my_stages + (size_t)j * kStage;
     const int64_t s0 = t0 + base;           // lane 0's first sample; its 4-float chunk starts the window
     const int k4 = (int)((s0 >> 2) & 7);    // the view whose rows start at that chunk
@@ -193,7 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   // stage into slot p of set `set` and reloads the stage; false on a timeout
   // (the window is then left unwritten and the block reports the error).
   auto write_window = [&](int c, int set) -> bool {
-    const int m = (c - p) / kLead, j = m % kWS;
+    const int m = mb + (c - p) / kLead, j = m % kWS;
     const int nch = __shfl_sync(0xffffffffu, (int)((uint32_t)__ldg(&gdesc[c].y) >> 24), 0);
     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&H.sfull[warp][j], (uint32_t)((m / kWS) & 1), kWaitLimitCycles)))
       return false;
@@ -320,14 +330,13 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   // no TMA may still be landing when the stage area is reused or the block
   // leaves (after a timeout some loads may not have been consumed)
   if (lane == 0) {
-    for (int m = max(0, issued - kWS); m < issued; ++m)
+    for (int m = mb + max(0, issued - kWS); m < mb + issued; ++m)
       (void)mbar_wait_bounded(&H.sfull[warp][m % kWS], (uint32_t)((m / kWS) & 1), kWaitLimitCycles);
   }
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
-  if (warp == 0) tmem_dealloc(H.tbase, kCols);
-  if (H.failed) return;
+  if (H.failed) return false;
 
   // ------------------------------------------------------------ epilogue
   // trial-major tile of 16-byte chunks; chunk k4 of row r sits at k4 ^ (r & 7)
@@ -359,6 +368,51 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
       if (t + 3 < a.n_out) o[3] = x.w;
     }
   }
+  // the next tile of a persistent block loads into this area again
+  __syncthreads();
+  return true;
+}
+
+template <bool WEIGHTED>
+__global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_constant__ Tmw9Maps maps, FwdArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Hdr& H = *reinterpret_cast<Hdr*>(smem_raw);
+  const uint32_t sbase = smem_u32(smem_raw);
+  unsigned char* stages = smem_raw + (((sbase + kHdr + 1023u) & ~1023u) - sbase);
+  // warp-uniform values go through a lane-0 broadcast, which lets the
+  // compiler keep them (and the TMEM addresses built from them) in uniform
+  // registers instead of moving each address over before each TMEM access
+  const int warp = __shfl_sync(0xffffffffu, (int)threadIdx.x >> 5, 0);
+  tmw9_setup(H, warp);
+  (void)tmw9_tile<WEIGHTED>(maps, a, blockIdx.x, blockIdx.y, 0, H, stages, warp);
+  tmw9_teardown(H, warp);
+}
+
+// Persistent form for batches: the block takes tiles of many beams from the
+// work list (see BatchWork; each beam's eight views sit in w.maps) until it is
+// exhausted; its Tensor Memory, stages and barriers carry over from tile to
+// tile.
+__global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_persistent(const __grid_constant__ BatchWork w) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Hdr& H = *reinterpret_cast<Hdr*>(smem_raw);
+  const uint32_t sbase = smem_u32(smem_raw);
+  unsigned char* stages = smem_raw + (((sbase + kHdr + 1023u) & ~1023u) - sbase);
+  const int warp = __shfl_sync(0xffffffffu, (int)threadIdx.x >> 5, 0);
+  __shared__ int item_s;
+  tmw9_setup(H, warp);
+  int mb = 0;
+  while (true) {
+    WorkItem it;
+    if (!next_item(w, item_s, it)) break;
+    const BatchBeam& bm = w.beams[it.beam];  // kernel parameters
+    const Tmw9Maps& maps = static_cast<const Tmw9Maps*>(w.maps)[it.beam];
+    // the beam's views live in global memory: fetch them before the first loads
+    if (threadIdx.x < kMaps) prefetch_tensormap(&maps.m[threadIdx.x]);
+    const bool ok = tmw9_tile<false>(maps, bm.a, it.x, it.y, mb, H, stages, warp);
+    mb += own_channels(bm.a.C, warp >> 2);
+    if (__syncthreads_or(!ok)) break;
+  }
+  tmw9_teardown(H, warp);
 }
 
 // ------------------------------------------------------------------- launch
@@ -440,6 +494,16 @@ cudaError_t launch_tmw9(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a,
   kern<<<grid, kThreads, kSmem, s>>>(maps, a);
   return cudaGetLastError();
 }
+
+size_t tmw9_views_bytes() { return sizeof(Tmw9Maps); }
+
+bool tmw9_encode_views(const FwdArgs& a, void* out) {
+  if (a.nine_desc == nullptr || !tmw9_accepts_avail(a.in, a.in_stride, a.in_avail, a.n_in)) return false;
+  return encode_views(static_cast<Tmw9Maps*>(out), a);
+}
+
+const void* tmw9_persistent_kernel() { return (const void*)fwd_tmw9_persistent; }
+const void* tmw9_plain_kernel() { return (const void*)fwd_tmw9_kernel<false>; }
 
 std::vector<TileConfig> tmw9_menu(dd_dtype dtype) {
   std::vector<TileConfig> v;

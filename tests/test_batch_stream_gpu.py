@@ -103,6 +103,69 @@ def test_batch_tune_once_per_setup(dd, tmp_path):
     batch.close()
 
 
+def test_persistent_groups_with_mixed_beams(dd):
+    """Persistent launches: several beams share each configuration (staged
+    float on LOFAR-grid beams of different trial spreads, so different staged
+    pitches; packed uint8; the 9-trial Tensor-Memory kernel), so one launch
+    runs the tiles of beams of different sizes back to back in the same
+    blocks.  The batch equals solo launches bit for bit, equals the oracle,
+    and equals the one-launch-per-beam batch; a second run replays the graph."""
+    rng = np.random.default_rng(5)
+    beams, force = [], []
+    for b in range(5):                      # LOFAR grid, float, one staged shape
+        C = int(rng.choice([32, 64]))
+        s = synth.Setup(f"st{b}", C, 138.0, 6.25 / C, 5e-6, 0.0, 0.01 * (b + 1), int(rng.choice([24, 40, 64])),
+                        int(rng.integers(2500, 7000)))
+        beams.append((s, "f32"))
+        force.append("staged_d8_t1024_c4_s3")
+    for b in range(4):                      # Apertif grid, uint8, one packed shape
+        C = int(rng.choice([64, 256]))
+        s = synth.Setup(f"u{b}", C, 1420.0, 300.0 / C, 50e-6, 0.0, 0.25, int(rng.choice([16, 48])),
+                        int(rng.integers(2000, 9000)))
+        beams.append((s, "u8"))
+        force.append("u8pk_w8x1_d2_c32_st3")
+    for b in range(3):                      # Apertif grid, float, the Tensor-Memory kernel
+        C = int(rng.choice([64, 256]))
+        s = synth.Setup(f"t{b}", C, 1420.0, 300.0 / C, 50e-6, 0.0, 0.25, int(rng.choice([18, 45])),
+                        int(rng.integers(3000, 9000)))
+        beams.append((s, "f32"))
+        force.append("tmw9_f32_d9_t4096")
+    plans, xs, hosts = _inputs(dd, beams, 40)
+    for p, name in zip(plans, force):
+        assert name in p.configs(), (p, name)
+        p.select(name)
+    batch = dd.Batch(plans)
+    batch.set_persistent(2)                      # every group persistent, whatever its kind
+    outs = [torch.full((p.n_dm, p.n_out), -1, dtype=p.out_dtype, device="cuda") for p in plans]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        batch.run(xs, outs, stream=stream)       # upload, capture, launch
+        batch.run(xs, outs, stream=stream)       # replay
+    stream.synchronize()
+    for (s, dt), p, x, h, o in zip(beams, plans, xs, hosts, outs):
+        assert p.device_status() == 0, s.name
+        assert torch.equal(o, p.forward(x)), s.name
+        ref, scale = oracle_window(oracle_table(s), h, dt, 0, s.n_dm, 0, s.n_out)
+        assert_parity(o.cpu().numpy(), ref, scale, dt, where=f"persistent batch {s.name}")
+    for mode in (0, 1):                          # one launch per beam; the kinds' defaults
+        batch.set_persistent(mode)
+        outs2 = [torch.full_like(o, -1) for o in outs]
+        with torch.cuda.stream(stream):
+            batch.run(xs, outs2, stream=stream)
+        stream.synchronize()
+        assert all(torch.equal(o, o2) for o, o2 in zip(outs, outs2)), mode
+    # tuning times each persistent group against its beams' own launches and
+    # keeps the faster form; results stay the same
+    batch.tune(budget_s=0.0)
+    outs3 = [torch.full_like(o, -1) for o in outs]
+    with torch.cuda.stream(stream):
+        batch.run(xs, outs3, stream=stream)
+    stream.synchronize()
+    for p, x, o in zip(plans, xs, outs3):
+        assert torch.equal(o, p.forward(x))
+    batch.close()
+
+
 def test_batch_rejects_unaligned(dd):
     s = synth.Setup("una", 32, 1420.0, 2.0, 50e-6, 0.0, 0.25, 16, 1000)
     p = dd.Plan.from_setup(s, "f32")
