@@ -155,8 +155,10 @@ __device__ __forceinline__ int own_channels(int C, int p) { return C > p ? (C - 
 // this warp's own channels of the block's earlier tiles (a persistent block
 // runs tile after tile): the warp's m-th own channel of this tile is its
 // (mb + m)-th, which fixes its stage and that stage's barrier phase.  False
-// after a timeout (reported in the status word; no output written).
-template <bool WEIGHTED>
+// after a timeout (reported in the status word; no output written).  A
+// block's last tile (LAST) frees the Tensor Memory as soon as the sums are in
+// registers and skips the barrier that guards the stage area for a next tile.
+template <bool WEIGHTED, bool LAST>
 __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a, int g, int ty, int mb, Hdr& H,
                                           unsigned char* stages, int warp) {
   const int tid = threadIdx.x, lane = tid & 31;
@@ -336,6 +338,7 @@ __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a
   tmem_fence_before_sync();
   __syncthreads();
   tmem_fence_after_sync();
+  if (LAST && warp == 0) tmem_dealloc(H.tbase, kCols);
   if (H.failed) return false;
 
   // ------------------------------------------------------------ epilogue
@@ -369,7 +372,7 @@ __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a
     }
   }
   // the next tile of a persistent block loads into this area again
-  __syncthreads();
+  if (!LAST) __syncthreads();
   return true;
 }
 
@@ -384,8 +387,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   // registers instead of moving each address over before each TMEM access
   const int warp = __shfl_sync(0xffffffffu, (int)threadIdx.x >> 5, 0);
   tmw9_setup(H, warp);
-  (void)tmw9_tile<WEIGHTED>(maps, a, blockIdx.x, blockIdx.y, 0, H, stages, warp);
-  tmw9_teardown(H, warp);
+  (void)tmw9_tile<WEIGHTED, true>(maps, a, blockIdx.x, blockIdx.y, 0, H, stages, warp);
 }
 
 // Persistent form for batches: the block takes tiles of many beams from the
@@ -408,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_persistent(const __grid_
     const Tmw9Maps& maps = static_cast<const Tmw9Maps*>(w.maps)[it.beam];
     // the beam's views live in global memory: fetch them before the first loads
     if (threadIdx.x < kMaps) prefetch_tensormap(&maps.m[threadIdx.x]);
-    const bool ok = tmw9_tile<false>(maps, bm.a, it.x, it.y, mb, H, stages, warp);
+    const bool ok = tmw9_tile<false, false>(maps, bm.a, it.x, it.y, mb, H, stages, warp);
     mb += own_channels(bm.a.C, warp >> 2);
     if (__syncthreads_or(!ok)) break;
   }
