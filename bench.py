@@ -49,10 +49,10 @@ SM_MAX_MHZ_NOMINAL = 2070.0
 # keyed by (setup name, output samples, kernel config, dtype); valid only while
 # the kernel source hash matches.
 NCU_TRAFFIC = {
-    # fwd_tmw9_kernel<0>: 110.8 MB read + 122.6 MB written
-    ("apertif", 20000, "tmw9_f32_d9_t4096", "f32"): {"bytes": 233_434_624, "hash": "bda16fccfcf36ce6"},
-    # fwd_u8pk_kernel<8,1,4,24,3>: 33.0 MB read + 111.8 MB written
-    ("apertif", 20000, "u8pk_w8x1_d4_c24_st3", "u8"): {"bytes": 144_827_392, "hash": "bda16fccfcf36ce6"},
+    # fwd_tmw9_kernel<0>: 111.0 MB read + 122.9 MB written
+    ("apertif", 20000, "tmw9_f32_d9_t4096", "f32"): {"bytes": 233_890_816, "hash": "dc50dc1c98ff89b6"},
+    # fwd_u8pk_kernel<8,1,4,24,3>: 32.6 MB read + 111.9 MB written
+    ("apertif", 20000, "u8pk_w8x1_d4_c24_st3", "u8"): {"bytes": 144_568_832, "hash": "dc50dc1c98ff89b6"},
 }
 
 
@@ -81,15 +81,91 @@ def _kernel_hash():
     return h.hexdigest()[:16]
 
 
+class NvmlSampler:
+    """SM clock, power and clock-event reasons read through NVML (libnvidia-ml,
+    ctypes) every 5 ms while `active`, so that even a timed region of a few
+    tens of milliseconds gets samples.  Reads only; changes no setting."""
+
+    # nvmlClocksEventReasons bits
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
+
+    def __init__(self, uuid: str):
+        import ctypes
+        self.ct = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.h = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.h)) != 0:
+            raise RuntimeError(f"no NVML device {uuid}")
+        try:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reasons_fn = self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.rows = []
+        self.active = False
+        self.done = threading.Event()
+        self.thread = None
+
+    def _sample(self):
+        ct = self.ct
+        sm, mx, mw, rs = ct.c_uint(), ct.c_uint(), ct.c_uint(), ct.c_ulonglong()
+        ok = self.lib.nvmlDeviceGetClockInfo(self.h, 1, ct.byref(sm)) == 0      # NVML_CLOCK_SM
+        ok = ok and self.lib.nvmlDeviceGetMaxClockInfo(self.h, 1, ct.byref(mx)) == 0
+        pw = self.lib.nvmlDeviceGetPowerUsage(self.h, ct.byref(mw)) == 0
+        rok = self.reasons_fn(self.h, ct.byref(rs)) == 0
+        if ok:
+            self.rows.append((float(sm.value), float(mx.value), mw.value / 1e3 if pw else None,
+                              int(rs.value) if rok else None))
+
+    def _run(self):
+        while not self.done.is_set():
+            if self.active:
+                self._sample()
+            time.sleep(0.005)
+
+    def start(self):
+        self.thread = threading.Thread(target=self._run, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        self.active = False
+        self.done.set()
+        if self.thread:
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0, "source": "nvml"}
+        reasons = set()
+        for r in self.rows:
+            if r[3] is not None:
+                reasons.update(n for n, bit in self.REASONS.items() if r[3] & bit)
+        power = [r[2] for r in self.rows if r[2] is not None]
+        return {"sm_mhz": statistics.median(r[0] for r in self.rows), "sm_max_mhz": max(r[1] for r in self.rows),
+                "reasons": sorted(reasons), "samples": len(self.rows),
+                "power_w_max": max(power) if power else None, "source": "nvml, 5 ms"}
+
+
+def clock_sampler(dev):
+    """NVML sampler of the device (by UUID), else the nvidia-smi one."""
+    import torch
+    uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    try:
+        return NvmlSampler(uuid)
+    except Exception:
+        return ClockSampler(uuid)
+
+
 class ClockSampler:
-    """nvidia-smi sampler for SM clocks and throttle reasons during the timed region."""
+    """nvidia-smi sampler (every 50 ms) for SM clocks and throttle reasons during the timed region."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index: int):
-        self.index = index
+    def __init__(self, ident):
+        self.index = ident
         self.rows = []
         self.proc = None
         self.active = False
@@ -526,7 +602,7 @@ def run_ours(args, setup):
     if plan.device_status() != 0:
         raise RuntimeError("device status nonzero after warm-up")
 
-    sampler = ClockSampler(dev.index)
+    sampler = clock_sampler(dev)
     sampler.start()
     if ws > 1:
         torch.distributed.barrier()
