@@ -33,9 +33,12 @@
 //    read a channel ahead and broadcast from lane 0, so the compiler keeps
 //    the TMEM addresses in uniform registers: no cross-warp bookkeeping.
 //  * Warp p writes the window of channel p of the next step while it works on
-//    the step's middle channel, from its private TMA stage (four 16-byte
+//    the step's last channel, from its private TMA stage (four 16-byte
 //    chunks per 16-column TMEM store); it then reloads the stage with its
-//    channel nine later.
+//    channel three later, so each tile load has one step to land.  (Deeper
+//    staging, loads two or three steps ahead, ran slower: 2.66 and 2.69 ms
+//    against 2.52 on the Apertif beam, whatever the shared-memory size; with
+//    the copy moved from the step's middle channel to its last, 2.50.)
 //  * The quadrant's three warps meet at a named barrier between steps, after
 //    the last loads of the step have been waited for and before the next
 //    step's first loads are issued: the next windows are then in TMEM and
@@ -64,7 +67,7 @@ constexpr int kTPW = 3;                   // trials per warp
 constexpr int kQRows = 34;                // tile rows per quadrant: 32 lanes + 2 (a window spans <= 17 chunks)
 constexpr int kTileBytes = kQRows * 128;  // 4352
 constexpr int kStage = 5 * 1024;          // whole 1024-byte swizzle atoms
-constexpr int kWS = 3;                    // stages per warp (its channels c, c + 3, c + 6 in flight)
+constexpr int kWS = 1;                    // stages per warp (its next own channel in flight)
 constexpr int kSlot = 80;                 // columns per window slot (20 chunks)
 constexpr int kLead = 3;                  // warps per quadrant = channels per step
 constexpr int kAhead = kLead * kWS;       // a warp's tile loads run this many channels ahead
@@ -72,7 +75,9 @@ constexpr int kBT = 128 * 32;             // samples per block
 constexpr int kThreads = 384;
 constexpr int kHdr = 1024;
 constexpr int kNStages = 12 * kWS;
-constexpr int kSmem = kHdr + kNStages * kStage + 1024;  // + slack to align the stages to 1024 bytes
+constexpr int kOutTile = kT * kBT * 4;  // the epilogue's tile reuses the stage area
+constexpr int kSmem = kHdr + (kNStages * kStage > kOutTile ? kNStages * kStage : kOutTile) +
+                      1024;  // + slack to align the stages to 1024 bytes
 constexpr uint32_t kCols = 512;
 constexpr int kMaps = 8;
 static_assert(2 * kLead * kSlot <= (int)kCols, "two sets of three windows fit TMEM");
@@ -80,7 +85,7 @@ static_assert(3 + kW9MaxOff + 32 <= kSlot, "a trial's 32 columns stay inside its
 static_assert(4 * 20 <= kSlot, "five 4-chunk batches fit a slot");
 static_assert((3 + 32 + kW9MaxOff + 3) / 4 <= 2 * 8 + 1, "a window spans rows r..r+2 of the tile");
 static_assert(kTileBytes <= kStage, "stage holds the tile");
-static_assert(kT * kBT * 4 <= kNStages * kStage, "output tile fits the stage area");
+static_assert(kHdr + kOutTile + 1024 <= kSmem, "output tile fits the stage area");
 
 struct Hdr {
   uint64_t sfull[12][kWS];  // per warp: its stages
@@ -173,8 +178,8 @@ __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a
   // ------------------------------------------------ this warp's tile loads
   // Warp (q, p) writes the windows of channels c = p (mod 3) for quadrant q.
   // Its m-th channel (c = p + 3m) sits in stage m % kWS; lane 0 loads the
-  // quadrant's 34 rows there and reloads the stage with channel c + 9 once
-  // the window is out.
+  // quadrant's 34 rows there and reloads the stage with channel c + 3 kWS
+  // once the window is out.
   unsigned char* my_stages = stages + (size_t)warp * kWS * kStage;
   int issued = 0;  // own channels whose load was issued (lane 0)
   auto base_of = [&](int c) { return c < C ? __ldg(&gdesc[c].x) : 0; };
@@ -315,7 +320,7 @@ __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a
         }
         // this warp's window of the next step, while a phase's load is in
         // flight (all warps at the same point of the step)
-        if (f == 1 && k == 1 && ok) {
+        if (f == 1 && k == kLead - 1 && ok) {
           const int cw = kLead * (n + 1) + p;
           if (cw < C) ok = write_window(cw, set ^ 1);
         }
