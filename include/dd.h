@@ -355,11 +355,9 @@ dd_status dd_batch_run(dd_batch_t batch, const void* const* ins, const int64_t* 
 dd_status dd_batch_tune(dd_batch_t batch, double budget_s, const char* db_path, int32_t* n_tuned);
 /* Which configuration groups dd_batch_run gives one persistent launch:
  * mode 0: none (one launch per beam); mode 1 (the default): those that
- * dd_batch_tune measured faster than their beams' own launches, and, untimed,
- * groups of the 9-trial Tensor-Memory kernel and of packed-uint8 shapes with
- * at most two trials per warp (the kinds that measured so on GB300); mode 2:
- * every group that can have one.  DD_ERR_ARG for another mode.  The next
- * dd_batch_run records its graph again. */
+ * dd_batch_tune measured faster than their beams' own launches (none before
+ * a tune); mode 2: every group that can have one.  DD_ERR_ARG for another
+ * mode.  The next dd_batch_run records its graph again. */
 dd_status dd_batch_set_persistent(dd_batch_t batch, int32_t mode);
 dd_status dd_batch_destroy(dd_batch_t batch);
 

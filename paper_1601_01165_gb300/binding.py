@@ -391,8 +391,8 @@ class Batch:
 
     def set_persistent(self, mode: int = 1):
         """dd_batch_set_persistent: 0 (or False) one launch per beam; 1 (or True, the
-        default) persistent launches where tuning measured them faster, else by kernel
-        kind; 2 a persistent launch for every group that can have one."""
+        default) persistent launches where dd_batch_tune measured them faster; 2 a
+        persistent launch for every group that can have one."""
         mode = int(mode)
         check(load().dd_batch_set_persistent(self._h, mode), "dd_batch_set_persistent")
 

@@ -11,8 +11,7 @@
 // blocks take the group's tiles, longest beam first, from a work counter
 // until none are left, so small beams fill the tails of large ones.  A group
 // runs that way where dd_batch_tune measured it faster than its beams' own
-// launches (or, untimed, for the kernel kinds that measured so); other beams
-// get one launch each.  The launches are dealt to a few internal streams by
+// launches (or wherever it can, in mode 2); other beams get one launch each.  The launches are dealt to a few internal streams by
 // accumulated work.  dd_batch_run records, once per (pointer set, stream),
 // the fork from the caller's stream, the counter resets and launches, and the
 // join back; later runs with the same pointers replay the graph with a single
@@ -93,13 +92,15 @@ struct RunPlan {
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Does a group run as one persistent launch?  Mode 2: yes; mode 1: as
-// dd_batch_tune measured it, else by the configuration's kind.
-static bool group_persistent(const dd_batch_s* b, const std::string& key, const TileConfig& cfg) {
+// Does a group run as one persistent launch?  Mode 2: yes; mode 1: if
+// dd_batch_tune measured it faster than its beams' own launches (untimed
+// groups run one launch per beam: on GB300 no kind's persistent launch
+// measured reliably faster).
+static bool group_persistent(const dd_batch_s* b, const std::string& key) {
   if (b->mode == 2) return true;
   for (const auto& kv : b->choice)
     if (kv.first == key) return kv.second;
-  return persistent_by_default(cfg);
+  return false;
 }
 
 // Sort the beams into persistent groups and single launches for the given
@@ -125,7 +126,7 @@ static dd_status build_run(dd_batch_s* b, const void* const* ins, const int64_t*
     const int smem = persistent_smem(*cfg, p->dtype, cfg->pitch);
     const int per_sm = persistent_blocks_per_sm(*cfg, p->dtype, smem);
     const std::string key = cfg->name + (p->dtype == DD_U8_I32 ? "/u8/" : "/f32/") + std::to_string(per_sm);
-    if (per_sm < 1 || per_sm < plain_blocks_per_sm(*cfg, p->dtype, cfg->smem) || !group_persistent(b, key, *cfg)) {
+    if (per_sm < 1 || per_sm < plain_blocks_per_sm(*cfg, p->dtype, cfg->smem) || !group_persistent(b, key)) {
       rp.singles.push_back(k);
       continue;
     }

@@ -162,8 +162,6 @@ const TileConfig* resolve_config(const dd_plan_s* p, const FwdArgs& a, int cfg_o
 // the resident ones, which then take every item in turn).  TMW9 beams need their eight tensor maps in the work's `maps`
 // (tmw9_encode_views writes them, tmw9_views_bytes of them per beam).
 bool has_persistent(const TileConfig& cfg, dd_dtype dtype);
-// Whether a group of this configuration runs persistent when no timing says otherwise.
-bool persistent_by_default(const TileConfig& cfg);
 int persistent_smem(const TileConfig& cfg, dd_dtype dtype, int pitch);
 int persistent_blocks_per_sm(const TileConfig& cfg, dd_dtype dtype, int smem);
 int plain_blocks_per_sm(const TileConfig& cfg, dd_dtype dtype, int smem);

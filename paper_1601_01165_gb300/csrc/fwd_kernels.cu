@@ -788,17 +788,6 @@ static const void* kernel_of(const TileConfig& cfg, dd_dtype dtype, int* threads
   }
 }
 
-// Measured on GB300 against the same beams' own launches: the TMW9 and the
-// one- or two-trial-per-warp U8PK persistent launches ran as fast or faster;
-// STAGED (its arguments reloaded from shared memory in a kernel bound by
-// shared-memory bandwidth) and four-trial U8PK ran 2-5 % slower.
-bool persistent_by_default(const TileConfig& cfg) {
-  if (cfg.kind == Kind::TmW9) return true;
-  if (cfg.kind != Kind::U8Pk) return false;
-  const int nw = cfg.threads / 32, wt = cfg.bt / (32 * 28), wd = nw / wt;
-  return cfg.bd / wd <= 2;
-}
-
 bool has_persistent(const TileConfig& cfg, dd_dtype dtype) {
   int threads = 0;
   return (cfg.kind == Kind::Staged || cfg.kind == Kind::U8Pk || cfg.kind == Kind::TmW9) &&

@@ -147,7 +147,7 @@ def test_persistent_groups_with_mixed_beams(dd):
         assert torch.equal(o, p.forward(x)), s.name
         ref, scale = oracle_window(oracle_table(s), h, dt, 0, s.n_dm, 0, s.n_out)
         assert_parity(o.cpu().numpy(), ref, scale, dt, where=f"persistent batch {s.name}")
-    for mode in (0, 1):                          # one launch per beam; the kinds' defaults
+    for mode in (0, 1):                          # one launch per beam; untuned automatic choice
         batch.set_persistent(mode)
         outs2 = [torch.full_like(o, -1) for o in outs]
         with torch.cuda.stream(stream):
