@@ -133,6 +133,7 @@ class NvmlSampler:
         self.done.set()
         if self.thread:
             self.thread.join(timeout=2)
+        self.lib.nvmlShutdown()
 
     def summary(self):
         if not self.rows:
@@ -201,7 +202,8 @@ class ClockSampler:
 
     def summary(self):
         if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "source": "nvidia-smi, 50 ms"}
         sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
         mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -212,7 +214,8 @@ class ClockSampler:
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": sorted(reasons), "samples": len(self.rows),
-                "power_w_max": max((float(r[2]) for r in self.rows if _isnum(r[2])), default=None)}
+                "power_w_max": max((float(r[2]) for r in self.rows if _isnum(r[2])), default=None),
+                "source": "nvidia-smi, 50 ms"}
 
 
 def _pct(xs, q):
