@@ -238,8 +238,13 @@ dd_status dd_forward_host(dd_plan_t plan, const void* host_in, int64_t in_row_st
  * in       device float [channels][in_row_stride] (needed only for grad_w).
  * grad_w   device float[channels] or NULL to skip; overwritten.
  * The weight gradient is reduced deterministically (no float atomics): two
- * calls with the same inputs give bit-identical results.  It uses a scratch
- * buffer the plan allocates on first use.
+ * calls with the same inputs give bit-identical results.  With grad_in NULL,
+ * on a float plan that offers the 9-trial Tensor-Memory kernel and
+ * an `in` that kernel takes (16-byte aligned rows of dd_plan_in_stride), it
+ * is computed directly on that kernel's tiles (about twice the forward's
+ * time); otherwise from the transpose.  The two ways sum in different orders
+ * (both within the float tolerance of the exact result).  Either uses
+ * scratch buffers the plan allocates on first use.
  * Errors: DD_ERR_UNSUPPORTED on a uint8 plan, DD_ERR_ARG if both outputs are
  * NULL or grad_w is requested without `in`, DD_ERR_SHAPE, DD_ERR_NOMEM,
  * DD_ERR_CUDA.

@@ -13,7 +13,9 @@
 //   grad_in[c][u] = w[c] * G[c][u]
 //   grad_w[c]     = sum_i sum_t grad_out[i][t] in[c][t + d(c,i)] = sum_u in[c][u] G[c][u]
 // The weight gradient is one dot product per channel, reduced in a fixed
-// order (deterministic, no atomics).
+// order (deterministic, no atomics).  Requested alone, on plans and inputs
+// the 9-trial Tensor-Memory forward takes, it is computed directly on that
+// kernel's tiles instead (fwd_tmw9.cu), again in a fixed order.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -98,6 +100,28 @@ extern "C" dd_status dd_adjoint(dd_plan_t plan, const float* grad_out, int64_t g
   if (grad_in && gi_row_stride < plan->n_in) return set_error(DD_ERR_SHAPE, "dd_adjoint: gi_row_stride < n_in");
   if (grad_w && in_row_stride < plan->n_in) return set_error(DD_ERR_SHAPE, "dd_adjoint: in_row_stride < n_in");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+
+  // The weight gradient alone, on a plan and input layout the 9-trial
+  // Tensor-Memory forward takes: the forward's own tiles multiply grad_out
+  // with the input windows (about one forward's time, no transposed plan).
+  if (grad_w && !grad_in) {
+    const FwdArgs a = plan_args(plan, in, in_row_stride, nullptr, nullptr, 0, 0, plan->n_out);
+    const int64_t n = tmw9_wgrad_partials(a);
+    if (n > 0) {
+      if (plan->adj_wpart_floats < n) {
+        cudaFree(plan->adj_wpart);
+        plan->adj_wpart_floats = 0;
+        if (cudaMalloc(&plan->adj_wpart, (size_t)n * sizeof(float)) != cudaSuccess) {
+          plan->adj_wpart = nullptr;
+          return set_error(DD_ERR_NOMEM, "dd_adjoint: cannot allocate %lld floats of partial sums", (long long)n);
+        }
+        plan->adj_wpart_floats = n;
+      }
+      const cudaError_t e = launch_tmw9_wgrad(a, grad_out, go_row_stride, plan->adj_wpart, grad_w, s);
+      if (e != cudaSuccess) return set_cuda_error("dd_adjoint: weight gradient", e);
+      return DD_OK;
+    }
+  }
 
   dd_plan_s* q = nullptr;
   dd_status st = adjoint_plan(plan, &q);

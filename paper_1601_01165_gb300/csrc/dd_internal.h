@@ -169,6 +169,12 @@ cudaError_t launch_persistent(const TileConfig& cfg, dd_dtype dtype, const Batch
                               cudaStream_t s);
 size_t tmw9_views_bytes();
 bool tmw9_encode_views(const FwdArgs& a, void* out);
+// Weight gradient on the TMW9 tiles (fwd_tmw9.cu): the partial sums it
+// needs (floats; 0 if the plan or the input layout does not take TMW9), and
+// the launch (grad_out [n_dm][g_stride], the partials' scratch, grad_w [C]).
+int64_t tmw9_wgrad_partials(const FwdArgs& a);
+cudaError_t launch_tmw9_wgrad(const FwdArgs& a, const float* g, int64_t g_stride, float* partial, float* grad_w,
+                              cudaStream_t s);
 const void* tmw9_persistent_kernel();
 const void* tmw9_plain_kernel();
 // Validated forward launch (dd_api.cpp); cfg_override < 0 uses the plan's choice.
@@ -230,4 +236,6 @@ struct dd_plan_s {
   int64_t adj_pad_stride = 0;
   float* adj_g = nullptr;         // [C][adj_g_stride] unweighted transpose when grad_in is not requested
   int64_t adj_g_stride = 0;
+  float* adj_wpart = nullptr;     // per-warp shares of the weight gradient on the TMW9 tiles
+  int64_t adj_wpart_floats = 0;
 };

@@ -168,6 +168,7 @@ void free_plan_device(dd_plan_s* p) {
   p->h_events.clear();
   cudaFree(p->adj_pad);
   cudaFree(p->adj_g);
+  cudaFree(p->adj_wpart);
   if (p->adj) {
     free_plan_device(p->adj);
     delete p->adj;
@@ -181,6 +182,8 @@ void free_plan_device(dd_plan_s* p) {
   p->h_dev_w = nullptr;
   for (int k = 0; k < 5; ++k) p->h_streams[k] = nullptr;
   p->adj_pad = p->adj_g = nullptr;
+  p->adj_wpart = nullptr;
+  p->adj_wpart_floats = 0;
 }
 
 // Default configuration: the first valid entry of a preference list, in

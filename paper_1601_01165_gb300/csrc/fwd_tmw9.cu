@@ -123,6 +123,15 @@ struct Tmw9Maps {
   CUtensorMap m[kMaps];
 };
 
+// Weight-gradient form of the tile (see fwd_tmw9_wgrad_kernel): grad_out
+// [n_dm][g_stride] and the per-warp partial sums.
+struct WgradArgs {
+  const float* g;
+  int64_t g_stride;
+  float* partial;  // [C][n_part]: channel c's share from warp w of tile b at c * n_part + 12 b + w
+  int64_t n_part;
+};
+
 // Load phases of one channel: six, each loading 16 columns of one trial
 // (tcgen05.ld.32x32b.x16), trials in turn: phase f reads trial f % 3,
 // columns 16 (f / 3) .. + 16.
@@ -163,9 +172,11 @@ __device__ __forceinline__ int own_channels(int C, int p) { return C > p ? (C - 
 // after a timeout (reported in the status word; no output written).  A
 // block's last tile (LAST) frees the Tensor Memory as soon as the sums are in
 // registers and skips the barrier that guards the stage area for a next tile.
-template <bool WEIGHTED, bool LAST>
+template <bool WEIGHTED, bool LAST, bool GRADW = false>
 __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a, int g, int ty, int mb, Hdr& H,
-                                          unsigned char* stages, int warp) {
+                                          unsigned char* stages, int warp, const WgradArgs* wg = nullptr,
+                                          int tile = 0) {
+  static_assert(!(GRADW && WEIGHTED), "the weight gradient does not use the weights");
   const int tid = threadIdx.x, lane = tid & 31;
   const int q = warp & 3, p = warp >> 2;
   const int r = 32 * q + lane;  // TMEM lane of this thread
@@ -260,11 +271,39 @@ __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a
   quad_sync();
 
   // ------------------------------------------------------------ main loop
+  // forward: acc holds the sums; weight gradient: acc holds this thread's
+  // grad_out values (zero outside the output), and s the channel's products
   float acc[kTPW][32];
+  float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;  // two independent pairs: shorter add chains
+  float vstep[kLead];  // the step's channels' per-lane products (weight gradient)
+  int nl = 32;            // this lane's samples inside the output (weight gradient)
+  bool mask_lane = false;  // warp-uniform: this tile holds a lane that ends inside the output
+  if constexpr (GRADW) {
+    const int64_t tl = t0 + 32 * r;
+    nl = (int)max((int64_t)0, min((int64_t)32, a.n_out - tl));
+    mask_lane = t0 + kBT > a.n_out && a.n_out % 32 != 0;
+    const bool vec = (reinterpret_cast<uintptr_t>(wg->g) % 16 == 0) && (wg->g_stride % 4 == 0) && nl == 32;
 #pragma unroll
-  for (int jj = 0; jj < kTPW; ++jj)
+    for (int jj = 0; jj < kTPW; ++jj) {
+      const int i = i0 + kTPW * p + jj;
+      const float* gr = wg->g + (int64_t)min(i, a.n_dm - 1) * wg->g_stride + tl;
+      if (vec && i < a.n_dm) {
 #pragma unroll
-    for (int k = 0; k < 32; ++k) acc[jj][k] = 0.0f;
+        for (int k4 = 0; k4 < 8; ++k4) {
+          const float4 v = __ldg(reinterpret_cast<const float4*>(gr) + k4);
+          acc[jj][4 * k4] = v.x, acc[jj][4 * k4 + 1] = v.y, acc[jj][4 * k4 + 2] = v.z, acc[jj][4 * k4 + 3] = v.w;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[jj][k] = (i < a.n_dm && k < nl) ? __ldg(gr + k) : 0.0f;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int jj = 0; jj < kTPW; ++jj)
+#pragma unroll
+      for (int k = 0; k < 32; ++k) acc[jj][k] = 0.0f;
+  }
   float X[kPH], Y[kPH];
   uint32_t ta[kTPW];
   float wc = 1.0f;
@@ -306,7 +345,38 @@ __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a
           for (int jj = 0; jj < kTPW; ++jj) ta[jj] = trial_addr(slot_col, cols_n, jj);
           tmem_ld16(ta[ph_trial(0)] + ph_col(0), nxt);
         }
-        {
+        if constexpr (GRADW) {
+          const int jj = ph_trial(f), c0 = ph_col(f);
+          if (mask_lane) {
+            // in the lane that holds the output's last samples, the samples
+            // past the output read input past n_in (padding the caller owns,
+            // maybe not finite): they must not reach the sum
+#pragma unroll
+            for (int u = 0; u < kPH; ++u) cur[u] = c0 + u < nl ? cur[u] : 0.0f;
+          }
+#pragma unroll
+          for (int u = 0; u < kPH; u += 4) {
+            fma2v_rn(s0, s1, cur[u], cur[u + 1], acc[jj][c0 + u], acc[jj][c0 + u + 1]);
+            fma2v_rn(s2, s3, cur[u + 2], cur[u + 3], acc[jj][c0 + u + 2], acc[jj][c0 + u + 3]);
+          }
+          if (f == kNPH - 1) {
+            // the warp's shares of the step's channels, reduced together at
+            // the step's end (interleaved, in a fixed order) and stored by lane 0
+            vstep[k] = nl > 0 ? (s0 + s1) + (s2 + s3) : 0.0f;  // lanes past the output add nothing
+            s0 = s1 = s2 = s3 = 0.0f;
+            if (k == kLead - 1 || !more) {
+#pragma unroll
+              for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int kk = 0; kk <= k; ++kk) vstep[kk] += __shfl_xor_sync(0xffffffffu, vstep[kk], o);
+              if (lane == 0) {
+#pragma unroll
+                for (int kk = 0; kk <= k; ++kk)
+                  wg->partial[(int64_t)(c - k + kk) * wg->n_part + (int64_t)tile * 12 + warp] = vstep[kk];
+              }
+            }
+          }
+        } else {
           const int jj = ph_trial(f), c0 = ph_col(f);
 #pragma unroll
           for (int u = 0; u < kPH; u += 2) {
@@ -345,6 +415,7 @@ __device__ __forceinline__ bool tmw9_tile(const Tmw9Maps& maps, const FwdArgs& a
   tmem_fence_after_sync();
   if (LAST && warp == 0) tmem_dealloc(H.tbase, kCols);
   if (H.failed) return false;
+  if constexpr (GRADW) return true;  // the partials are out
 
   // ------------------------------------------------------------ epilogue
   // trial-major tile of 16-byte chunks; chunk k4 of row r sits at k4 ^ (r & 7)
@@ -393,6 +464,42 @@ __global__ void __launch_bounds__(kThreads, 1) fwd_tmw9_kernel(const __grid_cons
   const int warp = __shfl_sync(0xffffffffu, (int)threadIdx.x >> 5, 0);
   tmw9_setup(H, warp);
   (void)tmw9_tile<WEIGHTED, true>(maps, a, blockIdx.x, blockIdx.y, 0, H, stages, warp);
+}
+
+// Weight gradient of the forward (grad_w[c] = sum_i sum_t grad_out[i][t]
+// in[c][t + d(c, i)]) on the forward's tiles: each thread keeps its 96
+// grad_out values where the forward keeps its sums, multiplies them with the
+// same Tensor-Memory windows and adds the products of each channel; every
+// warp stores its share of each channel's sum (a fixed-order shuffle
+// reduction), and wgrad_reduce_kernel adds the shares in a fixed order.
+__global__ void __launch_bounds__(kThreads, 1)
+    fwd_tmw9_wgrad_kernel(const __grid_constant__ Tmw9Maps maps, FwdArgs a, WgradArgs wg) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  Hdr& H = *reinterpret_cast<Hdr*>(smem_raw);
+  const uint32_t sbase = smem_u32(smem_raw);
+  unsigned char* stages = smem_raw + (((sbase + kHdr + 1023u) & ~1023u) - sbase);
+  const int warp = __shfl_sync(0xffffffffu, (int)threadIdx.x >> 5, 0);
+  tmw9_setup(H, warp);
+  const int tile = (int)(blockIdx.y * gridDim.x + blockIdx.x);
+  (void)tmw9_tile<false, true, true>(maps, a, blockIdx.x, blockIdx.y, 0, H, stages, warp, &wg, tile);
+}
+
+// grad_w[c] = the sum of channel c's n_part shares: one block per channel,
+// each thread a strided subset in double, then a fixed reduction tree.
+__global__ void __launch_bounds__(256) wgrad_reduce_kernel(const float* __restrict__ partial, int64_t n_part,
+                                                          float* __restrict__ grad_w) {
+  __shared__ double red[256];
+  const int c = blockIdx.x;
+  const float* row = partial + (int64_t)c * n_part;
+  double sum = 0.0;
+  for (int64_t k = threadIdx.x; k < n_part; k += 256) sum += (double)row[k];
+  red[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) grad_w[c] = (float)red[0];
 }
 
 // Persistent form for batches: the block takes tiles of many beams from the
@@ -499,6 +606,30 @@ cudaError_t launch_tmw9(const TileConfig& cfg, dd_dtype dtype, const FwdArgs& a,
   dim3 grid((unsigned)((a.n_dm + kT - 1) / kT), (unsigned)((a.n_out + kBT - 1) / kBT));
   if (grid.y > 65535) return cudaErrorInvalidConfiguration;
   kern<<<grid, kThreads, kSmem, s>>>(maps, a);
+  return cudaGetLastError();
+}
+
+int64_t tmw9_wgrad_partials(const FwdArgs& a) {
+  if (a.nine_desc == nullptr || !tmw9_accepts_avail(a.in, a.in_stride, a.in_avail, a.n_in)) return 0;
+  const int64_t tiles = (int64_t)((a.n_dm + kT - 1) / kT) * ((a.n_out + kBT - 1) / kBT);
+  return tiles * 12 * a.C;
+}
+
+cudaError_t launch_tmw9_wgrad(const FwdArgs& a, const float* g, int64_t g_stride, float* partial, float* grad_w,
+                              cudaStream_t s) {
+  const int64_t n = tmw9_wgrad_partials(a);
+  if (n <= 0 || g == nullptr || partial == nullptr || grad_w == nullptr) return cudaErrorInvalidConfiguration;
+  Tmw9Maps maps;
+  if (!encode_views(&maps, a)) return cudaErrorInvalidValue;
+  auto kern = fwd_tmw9_wgrad_kernel;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmem);
+  if (e != cudaSuccess) return e;
+  dim3 grid((unsigned)((a.n_dm + kT - 1) / kT), (unsigned)((a.n_out + kBT - 1) / kBT));
+  if (grid.y > 65535) return cudaErrorInvalidConfiguration;
+  const int64_t n_part = n / a.C;
+  kern<<<grid, kThreads, kSmem, s>>>(maps, a, WgradArgs{g, g_stride, partial, n_part});
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  wgrad_reduce_kernel<<<a.C, 256, 0, s>>>(partial, n_part, grad_w);
   return cudaGetLastError();
 }
 

@@ -145,6 +145,15 @@ __device__ __forceinline__ void fma2_rn(float& a0, float& a1, float w, float b0,
       : "f"(b0), "f"(b1), "f"(w));
 }
 
+// Two independent fused multiply-adds of pairs, x_k * y_k + a_k with one
+// rounding each, in one instruction; each lane's result is fmaf's bit for bit.
+__device__ __forceinline__ void fma2v_rn(float& a0, float& a1, float x0, float x1, float y0, float y1) {
+  asm("{\n .reg .b64 a, x, y;\n mov.b64 a, {%0, %1};\n mov.b64 x, {%2, %3};\n mov.b64 y, {%4, %5};\n"
+      " fma.rn.f32x2 a, x, y, a;\n mov.b64 {%0, %1}, a;\n}\n"
+      : "+f"(a0), "+f"(a1)
+      : "f"(x0), "f"(x1), "f"(y0), "f"(y1));
+}
+
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"

@@ -57,6 +57,38 @@ def test_adjoint_and_wgrad_match_oracle(dd, setup):
     assert torch.equal(gw, gw2)
 
 
+@pytest.mark.parametrize("n_out", [1931, 8192], ids=["ragged", "whole-tiles"])
+def test_weight_gradient_alone_on_tmw9_tiles(dd, n_out):
+    """grad_w requested alone on a plan and input the 9-trial Tensor-Memory
+    forward takes runs on that kernel's tiles: the products of grad_out with
+    the input windows, summed per channel in a fixed order.  It matches the
+    oracle, the transposed-plan path (the combined call) within the fp32 bar,
+    and itself bit for bit.  NaN in the row padding past n_in must not reach
+    the sums (samples past the output are masked)."""
+    s = synth.Setup(f"wg-{n_out}", 1024, 1420.0, 0.29296875, 50e-6, 3.0, 0.25, 41, n_out)
+    plan = dd.Plan.from_setup(s, "f32")
+    assert "tmw9_f32_d9_t4096" in plan.configs()
+    d = oracle_table(s)
+    stride = plan.padded_in_stride()
+    x, _ = make_input(s, "f32", 11, plan.n_in, stride)
+    x[:, plan.n_in:] = np.nan
+    g = synth.noise_f32(12, s.n_dm, s.n_out)
+    xt, gt = torch.from_numpy(x).cuda(), torch.from_numpy(g).cuda()
+    _, gw = plan.adjoint(gt, x=xt, grad_in=False, grad_w=True)
+    _, gw_again = plan.adjoint(gt, x=xt, grad_in=False, grad_w=True)
+    _, gw_transposed = plan.adjoint(gt, x=xt, grad_in=True, grad_w=True)
+    torch.cuda.synchronize()
+    assert plan.device_status() == 0
+    assert torch.equal(gw, gw_again)
+    xs = np.ascontiguousarray(x[:, :plan.n_in])
+    refw = oracle.wgrad_f32(d, g, xs)
+    scalew = oracle.wgrad_f32(d, np.abs(g), np.abs(xs))
+    for got in (gw, gw_transposed):
+        errw = np.abs(got.cpu().numpy().astype(np.float64) - refw)
+        assert np.isfinite(errw).all()
+        assert (errw <= FP32_REL * scalew).all(), float((errw - FP32_REL * scalew).max())
+
+
 def test_adjoint_full_apertif_sampled(dd):
     """Full Apertif size: a sample of channels checked against the oracle on all DMs."""
     s = synth.APERTIF
