@@ -107,7 +107,9 @@ extern "C" dd_status dd_adjoint(dd_plan_t plan, const float* grad_out, int64_t g
   if (grad_w && !grad_in) {
     const FwdArgs a = plan_args(plan, in, in_row_stride, nullptr, nullptr, 0, 0, plan->n_out);
     const int64_t n = tmw9_wgrad_partials(a);
-    if (n > 0) {
+    // (12 partial sums per channel and tile: past 1 GiB of them, as for very
+    // long outputs, the transposed path below needs less memory)
+    if (n > 0 && n <= ((int64_t)1 << 28)) {
       if (plan->adj_wpart_floats < n) {
         cudaFree(plan->adj_wpart);
         plan->adj_wpart_floats = 0;
