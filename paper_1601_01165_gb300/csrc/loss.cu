@@ -7,7 +7,8 @@
 // ties).  For the best row i*, t*:
 //   d z[t*] / d b[t] = ((t == t*) - 1/nb) / s - z[t*] z[t] / (nb s)
 //   d loss / d x[i*][u] = -sum over t in [u-7, u] of d z[t*] / d b[t].
-// All sums in double; each row is one block with a fixed reduction tree.
+// Each thread sums in two-float arithmetic (about 48 bits), each block in
+// double; each row is one block with a fixed reduction tree.
 #include <cuda_runtime.h>
 
 #include <cfloat>
@@ -47,16 +48,74 @@ __device__ double block_sum(double v, double* red) {
   return r;
 }
 
-// One block per row: mean, sd, best S/N and where it is.  Each thread takes
-// a contiguous run of boxcar starts and slides the window, b[t] = b[t-1] +
-// (x[t+7] - x[t-1]) in double.  A sum of a few floats is exact in double while
-// the row's values span less than 2^26 in magnitude, so then b equals the
-// direct 8-term sum.  Pass 1: the sum of b and the largest b (first t);
-// pass 2: the variance about the mean; the best S/N is (b_max - mean) / sd
-// with one division.  S/N is monotonic in b, so the first maximum of S/N lies
-// among the starts whose b is within rounding of b_max; pass 3 takes the first
-// start up to that t whose S/N equals the best (a different t only when two
-// sums round to one S/N).
+// Two-float ("double-float") numbers: h + l with |l| <= ulp(h) / 2, about 48
+// significant bits.  Double arithmetic is slow on this GPU's SMs; these
+// sums use a few single-precision operations each (Knuth's two-sum, Dekker's
+// fast two-sum and an FMA-based exact product), with explicit round-to-nearest
+// intrinsics so that the compiler neither fuses nor reorders them.
+struct DF {
+  float h, l;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+  const DF s = two_sum(a.h, b);
+  return fast_two_sum(s.h, __fadd_rn(s.l, a.l));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = two_sum(a.h, b.h);
+  const DF t = two_sum(a.l, b.l);
+  const DF u = fast_two_sum(s.h, __fadd_rn(s.l, t.h));
+  return fast_two_sum(u.h, __fadd_rn(u.l, t.l));
+}
+
+// d * d for a two-float d, as a two-float (the low part's square is dropped)
+__device__ __forceinline__ DF df_sqr(DF d) {
+  const float p = __fmul_rn(d.h, d.h);
+  const float e = __fmaf_rn(d.h, d.h, -p);
+  return fast_two_sum(p, __fmaf_rn(__fmul_rn(2.0f, d.h), d.l, e));
+}
+
+__device__ __forceinline__ DF df_of(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+__device__ __forceinline__ double df_value(DF a) { return (double)a.h + (double)a.l; }
+
+// a > b for normalised two-floats
+__device__ __forceinline__ bool df_gt(DF a, DF b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
+
+// The boxcar starting at t as a two-float (exact while the 8 values span
+// less than 2^24 or so in magnitude).
+__device__ __forceinline__ DF boxcar_df(const float* row, int64_t t) {
+  DF b{0.0f, 0.0f};
+#pragma unroll
+  for (int k = 0; k < kBox; ++k) b = df_add_f(b, __ldg(row + t + k));
+  return b;
+}
+
+// One block per row: mean, sd, best S/N and where it is.  Thread j takes
+// the boxcar starts j, j + NT, ... (coalesced loads; each boxcar summed from
+// its 8 values in two-float arithmetic, exact while they span less than 2^24
+// or so in magnitude, so b equals the direct 8-term sum and its double
+// value).  Pass 1: the sum of b and the largest b (first t); pass 2: the
+// variance about the mean (each thread's sums in two-float, the block's in
+// double); the best S/N is (b_max - mean) / sd in double.  S/N is monotonic
+// in b, so the first maximum of S/N lies among the starts whose b is within
+// rounding of b_max; pass 3 takes the first start before that t whose S/N
+// equals the best (a different t only when two sums round to one S/N).
 template <int NT>
 __global__ void __launch_bounds__(NT) snr_rows_kernel(const float* __restrict__ x, int64_t stride, int64_t n_cols,
                                                       RowStat* __restrict__ stats) {
@@ -66,26 +125,20 @@ __global__ void __launch_bounds__(NT) snr_rows_kernel(const float* __restrict__ 
   const int i = blockIdx.x;
   const float* row = x + (int64_t)i * stride;
   const int64_t nb = n_cols - kBox + 1;
-  const int64_t per = (nb + NT - 1) / NT;
-  const int64_t t_begin = min(nb, (int64_t)threadIdx.x * per), t_end = min(nb, t_begin + per);
 
   // pass 1: sum and largest boxcar
-  double s = 0.0, bmax = -DBL_MAX;
+  DF s{0.0f, 0.0f}, bmax{-FLT_MAX, 0.0f};
   int64_t tmax = -1;
-  if (t_begin < t_end) {
-    double b = boxcar(row, t_begin);
-    for (int64_t t = t_begin;;) {
-      s += b;
-      if (b > bmax) {  // t increases, so the first maximum is kept
-        bmax = b;
-        tmax = t;
-      }
-      if (++t >= t_end) break;
-      b += (double)__ldg(row + t + kBox - 1) - (double)__ldg(row + t - 1);
+  for (int64_t t = threadIdx.x; t < nb; t += NT) {
+    const DF b = boxcar_df(row, t);
+    s = df_add(s, b);
+    if (tmax < 0 || df_gt(b, bmax)) {  // t increases, so the first maximum is kept
+      bmax = b;
+      tmax = t;
     }
   }
-  const double mean = block_sum<NT>(s, red) / (double)nb;
-  zbest[threadIdx.x] = bmax;
+  const double mean = block_sum<NT>(df_value(s), red) / (double)nb;
+  zbest[threadIdx.x] = df_value(bmax);
   tbest[threadIdx.x] = tmax;
   __syncthreads();
   for (int h = NT / 2; h > 0; h >>= 1) {
@@ -105,17 +158,10 @@ __global__ void __launch_bounds__(NT) snr_rows_kernel(const float* __restrict__ 
   __syncthreads();
 
   // pass 2: variance about the mean
-  double v = 0.0;
-  if (t_begin < t_end) {
-    double b = boxcar(row, t_begin);
-    for (int64_t t = t_begin;;) {
-      const double d = b - mean;
-      v += d * d;
-      if (++t >= t_end) break;
-      b += (double)__ldg(row + t + kBox - 1) - (double)__ldg(row + t - 1);
-    }
-  }
-  const double sd = sqrt(block_sum<NT>(v, red) / (double)nb);
+  const DF neg_mean = df_of(-mean);
+  DF v{0.0f, 0.0f};
+  for (int64_t t = threadIdx.x; t < nb; t += NT) v = df_add(v, df_sqr(df_add(boxcar_df(row, t), neg_mean)));
+  const double sd = sqrt(block_sum<NT>(df_value(v), red) / (double)nb);
   if (!(sd > 0.0)) {
     if (threadIdx.x == 0) stats[i] = RowStat{-DBL_MAX, mean, sd, -1};
     return;
@@ -125,16 +171,16 @@ __global__ void __launch_bounds__(NT) snr_rows_kernel(const float* __restrict__ 
   // pass 3: the first start before t_top with the same S/N, if any
   const double b_cut = b_top - 1e-12 * (fabs(b_top - mean) + fabs(b_top));
   int64_t tf = t_top;
-  const int64_t t_stop = min(t_end, t_top);
-  if (t_begin < t_stop) {
-    double b = boxcar(row, t_begin);
-    for (int64_t t = t_begin;;) {
-      if (b >= b_cut && (b - mean) / sd == z_top) {
+  // below cut_f (two float steps under b_cut) a two-float value is surely below b_cut
+  const float cut_f = nextafterf(nextafterf((float)b_cut, -FLT_MAX), -FLT_MAX);
+  for (int64_t t = threadIdx.x; t < t_top; t += NT) {
+    const DF b = boxcar_df(row, t);
+    if (b.h >= cut_f) {
+      const double bd = df_value(b);
+      if (bd >= b_cut && (bd - mean) / sd == z_top) {
         tf = t;
         break;
       }
-      if (++t >= t_stop) break;
-      b += (double)__ldg(row + t + kBox - 1) - (double)__ldg(row + t - 1);
     }
   }
   tbest[threadIdx.x] = tf;
