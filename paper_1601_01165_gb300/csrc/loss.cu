@@ -97,8 +97,9 @@ __device__ __forceinline__ double df_value(DF a) { return (double)a.h + (double)
 // a > b for normalised two-floats
 __device__ __forceinline__ bool df_gt(DF a, DF b) { return a.h > b.h || (a.h == b.h && a.l > b.l); }
 
-// The boxcar starting at t as a two-float (exact while the 8 values span
-// less than 2^24 or so in magnitude).
+// The boxcar starting at t as a two-float (exact while the 8 values' nonzero
+// magnitudes lie within a factor of about 2^21: 48 bits hold the sum of eight
+// 24-bit significands spread that far).
 __device__ __forceinline__ DF boxcar_df(const float* row, int64_t t) {
   DF b{0.0f, 0.0f};
 #pragma unroll
@@ -108,9 +109,9 @@ __device__ __forceinline__ DF boxcar_df(const float* row, int64_t t) {
 
 // One block per row: mean, sd, best S/N and where it is.  Thread j takes
 // the boxcar starts j, j + NT, ... (coalesced loads; each boxcar summed from
-// its 8 values in two-float arithmetic, exact while they span less than 2^24
-// or so in magnitude, so b equals the direct 8-term sum and its double
-// value).  Pass 1: the sum of b and the largest b (first t); pass 2: the
+// its 8 values in two-float arithmetic, exact while their nonzero magnitudes
+// lie within a factor of about 2^21, so b equals the direct 8-term sum and
+// its double value).  Pass 1: the sum of b and the largest b (first t); pass 2: the
 // variance about the mean (each thread's sums in two-float, the block's in
 // double); the best S/N is (b_max - mean) / sd in double.  S/N is monotonic
 // in b, so the first maximum of S/N lies among the starts whose b is within
